@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Throughput of the fermion part of the many-flavour HMC MD step on GB300.
+
+One step = one pass of the hot path on the 12^4 SF workload with 5
+pseudo-fermion fields (N_f = 10): link preparation for the current gauge
+field (SU(3) check, FP64/FP32/FP16 kernel copies), the blocked solves of
+Alg. 2 (X = Dhat^-1 Phi, Y = Dhat^-dag X to true relative residual 1e-10, FP32
+BiCGStab inner / FP64 defect-correction outer), odd-site reconstruction and
+the force F = sum_i f[x_i, y_i] of Eq. (3) with the FP64 momentum update.
+The metric is 5-RHS solves per second (a solve = X and Y for all 5 fields,
+plus the force), summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the same workload (bounded
+samples scaled to a full step).  Under torchrun every rank runs its own
+replica of the workload (the path has no exchange step); the time is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "5-RHS SF Wilson solves/s at true rel. residual 1e-10"
+UNIT = "solves/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("krylov_impl.cuh", "sf_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1009_5169_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(key):
+    """Per-launch DRAM bytes of the dslash kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dslash_traffic.json")) as f:
+            d = json.load(f)
+        e = d.get(key)
+        if e and e.get("kernel_hash") == _kernel_hash():
+            return e
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"sf_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1009_5169_gb300 import binding as sf
+    from paper_1009_5169_gb300 import inputs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = inputs.workload(args.workload)
+    lt = w.lattices[0]
+    nrhs, tol = w.nrhs, w.tol
+    U = lt.make_links()
+    phi = lt.make_sources(nrhs)
+    stream = torch.cuda.current_stream(dev)
+    U_d = torch.from_numpy(U).to(dev)
+    phi_d = torch.from_numpy(phi).to(dev)
+    X_d = torch.empty_like(phi_d)
+    Y_d = torch.empty_like(phi_d)
+    fshape = ((lt.T + 1) * lt.L ** 3, 4, 8)
+    F_d = torch.zeros(fshape, dtype=torch.float64, device=dev)
+    mom_d = torch.zeros(fshape, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, U_d, device=local_rank)
+    eps_md = 0.01
+
+    def step(Ub, ph, X, Y, F, mom):
+        lat.set_links(Ub)
+        info = sf.solve_block(lat, args.algo, ph, X, Y, tol=tol, maxiter=args.maxiter)
+        sf.fermion_force(lat, X, Y, F, mom, eps=eps_md)
+        return info
+
+    # fixed launches per step outside the solver: SU(3) check + link prep, and
+    # in the force: 2 packs, 2 odd-site hops, 1 force kernel
+    fixed_launches = 2 + 5
+    for _ in range(args.warmup):
+        info = step(U_d, phi_d, X_d, Y_d, F_d, mom_d)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    infos = []
+    for k in range(args.steps):
+        flush.zero_()                      # L2 flushed between steps (outside the timed step)
+        starts[k].record(stream)
+        info = step(U_d, phi_d, X_d, Y_d, F_d, mom_d)
+        ends[k].record(stream)
+        infos.append(info)
+        launches += info["kernel_launches"] + fixed_launches
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # accuracy of the last step, from the library's FP64 recomputation
+    last = infos[-1]
+    resid = max(max(last["true_resid"]), max(last["true_resid_y"]))
+
+    # ---------------- end to end through the public API with host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    U_h, phi_h = pin(U), pin(phi)
+    X_h, Y_h = torch.empty_like(phi_h).pin_memory(), torch.empty_like(phi_h).pin_memory()
+    F_h = torch.zeros(fshape, dtype=torch.float64).pin_memory()
+    mom_h = torch.zeros(fshape, dtype=torch.float64).pin_memory()
+    step(U_h, phi_h, X_h, Y_h, F_h, mom_h)
+    e2e_s = 0.0
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(U_h, phi_h, X_h, Y_h, F_h, mom_h)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nb = lambda a: a.numel() * a.element_size()
+    h2d = nb(U_h) + nb(phi_h) + nb(X_h) + nb(Y_h) + nb(mom_h)   # links, phi, X and Y into the force, mom
+    d2h = nb(X_h) + nb(Y_h) + nb(F_h) + nb(mom_h)
+    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---------------- roofline of the dominant kernel: the FP32 dslash (hop)
+    peak, peak_kind = _peaks()
+    prec = "fp32" if args.algo == "mixed_dc" else ("fp16" if args.algo == "mixed_dc_half" else "fp64")
+    TS, NR = lat.get_tuning(prec, nrhs)
+    Vh = lt.Vh
+    site_bytes = {"fp32": nrhs * 96 * 2 + 8 * 48, "fp16": nrhs * 52 * 2 + 8 * 24,
+                  "fp64": nrhs * 192 * 2 + 8 * 144}[prec]
+    alg_bytes = Vh * site_bytes
+    sf.wilson_hop_resident(lat, prec, nrhs, 1)
+    reps = 50
+    cold = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sf.wilson_hop_resident(lat, prec, nrhs, 1)
+        b.record(stream)
+        cold.append((a, b))
+    torch.cuda.synchronize()
+    t_cold = statistics.mean(a.elapsed_time(b) for a, b in cold) * 1e-3
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        sf.wilson_hop_resident(lat, prec, nrhs, 1)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_warm = a.elapsed_time(b) * 1e-3 / reps
+    achieved = alg_bytes / t_cold / 1e9
+    tr = _ncu_traffic(f"{args.workload}:{prec}")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "kernel": f"k_hop<{prec}> (dslash H_oe), TS={TS}, NR={NR}, L2 flushed before each launch",
+                "algorithmic_bytes_per_launch": alg_bytes, "launch_us": round(t_cold * 1e6, 2),
+                "l2_warm_launch_us": round(t_warm * 1e6, 2), "peak_kind": peak_kind}
+
+    # ---------------- dslash on a lattice larger than L2 (HBM-bound case)
+    hbm = None
+    if not args.no_hbm_case and rank == 0:
+        Lh, Th = 32, 24
+        Ub = inputs.links(Lh, Th, 0.2, inputs.SEED_BASE + 32, device=dev)
+        big = sf.Lattice(Lh, Th, 0.5, 0.13, 4.52, torch.from_numpy(Ub).to(dev), device=local_rank)
+        del Ub
+        res = {}
+        for p in ("fp32", "fp16"):
+            TSb, NRb = big.get_tuning(p, nrhs)
+            sf.wilson_hop_resident(big, p, nrhs, 1)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(20):
+                sf.wilson_hop_resident(big, p, nrhs, 1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) * 1e-3 / 20
+            Vhb = Lh ** 3 * (Th - 1) // 2
+            sb = {"fp32": nrhs * 96 * 2 + 8 * 48, "fp16": nrhs * 52 * 2 + 8 * 24}[p]
+            ab = Vhb * sb
+            trb = _ncu_traffic(f"hbm32x24:{p}")
+            res[p] = {"achieved": round(ab / t / 1e9, 1), "frac": round(ab / t / 1e9 / peak, 4),
+                      "launch_us": round(t * 1e6, 2), "algorithmic_bytes_per_launch": ab, "TS": TSb, "NR": NRb,
+                      "traffic": trb["dram_bytes_per_launch"] if trb else None}
+        big.close()
+        hbm = {"lattice": f"{Lh}^3x{Th} SF, 5 RHS (inputs larger than L2)", "unit": "GB/s", "peak": peak, **res}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer" if prec == "fp32" else prec,
+        "data": "synthetic (seeded SF gauge field exp(i eps H) and Gaussian pseudo-fermions)",
+        "config": {"workload": f"{args.workload}: {lt.L}^3x{lt.T} SF, eps {lt.eps}, kappa {lt.kappa}, "
+                               f"theta {lt.theta}, {nrhs} RHS, tol {tol}, X and Y solves + force",
+                   "algo": args.algo, "l2": "flushed between steps", "parallelism": f"replicas x{world}",
+                   "tiling": {"fp64": lat.get_tuning("fp64", nrhs), prec: (TS, NR)}},
+        "accuracy": {"max_true_rel_resid": resid, "sweeps_x": last["iters_outer"], "inner_iters_x": last["iters_inner"],
+                     "sweeps_y": last["iters_outer_y"], "inner_iters_y": last["iters_inner_y"]},
+        "roofline": roofline, "dslash_hbm": hbm, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+    }
+    lat.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------------------- oracle
+def _oracle_step_estimate(w, U, phi, calib, sample_iters):
+    """Time a bounded sample of the oracle on one pseudo-fermion field and
+    scale it to a full 5-field step.  calib holds the oracle's full-solve
+    iteration counts for one field (measured once)."""
+    import oracle
+    lt = w.lattices[0]
+    t0 = time.perf_counter()
+    x, it_x, _ = oracle.bicgstab(U, phi[:1], lt.L, lt.T, lt.theta, lt.kappa, tol=w.tol, maxiter=sample_iters)
+    y, it_y, _ = oracle.bicgstab(U, x, lt.L, lt.T, lt.theta, lt.kappa, tol=w.tol, maxiter=sample_iters,
+                                 dagger=True)
+    t1 = time.perf_counter()
+    oracle.force(U, x, y, lt.L, lt.T, lt.theta, lt.kappa)
+    t2 = time.perf_counter()
+    per_iter = (t1 - t0) / max(1, int(it_x[0]) + int(it_y[0]))
+    full = w.nrhs * (per_iter * (calib[0] + calib[1]) + (t2 - t1))
+    return full, (t2 - t0)
+
+
+def _oracle_calibrate(w, U, phi):
+    import oracle
+    lt = w.lattices[0]
+    x, it_x, _ = oracle.bicgstab(U, phi[:1], lt.L, lt.T, lt.theta, lt.kappa, tol=w.tol, maxiter=20000)
+    _, it_y, _ = oracle.bicgstab(U, x, lt.L, lt.T, lt.theta, lt.kappa, tol=w.tol, maxiter=20000, dagger=True)
+    return int(it_x[0]), int(it_y[0])
+
+
+def cpu_baseline(args, budget_s=20.0):
+    """The FP64 oracle as it stands on the host cores: one full solve pair of
+    one field calibrates the iteration counts; a bounded sample of iterations
+    plus one force gives the time of a 5-field step."""
+    import oracle
+    from paper_1009_5169_gb300 import inputs
+    w = inputs.workload(args.workload)
+    lt = w.lattices[0]
+    U = lt.make_links()
+    phi = lt.make_sources(w.nrhs)
+    t0 = time.perf_counter()
+    calib = _oracle_calibrate(w, U, phi)
+    tcal = time.perf_counter() - t0
+    est, used = _oracle_step_estimate(w, U, phi, calib, 40)
+    return {"value": round(1.0 / est, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one of the {w.nrhs} fields: full X and Y solves (calibration, {tcal:.1f}s, "
+                      f"{calib[0]}+{calib[1]} BiCGStab iterations) and 40+40 iterations plus one force "
+                      f"({used:.1f}s), scaled to {w.nrhs} fields",
+            "seconds_per_step": round(est, 3)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1009_5169_gb300 import inputs
+    w = inputs.workload(args.workload)
+    lt = w.lattices[0]
+    U = lt.make_links()
+    phi = lt.make_sources(w.nrhs)
+    calib = _oracle_calibrate(w, U, phi)
+    for _ in range(args.warmup):
+        _oracle_step_estimate(w, U, phi, calib, 10)
+    est = []
+    used = 0.0
+    for _ in range(args.steps):
+        e, u = _oracle_step_estimate(w, U, phi, calib, 10)
+        est.append(e)
+        used += u
+    sps = 1.0 / statistics.mean(est)
+    out = {"impl": "reference", "metric": METRIC, "value": round(sps, 6), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(est) * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": args.workload},
+           "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": round(sps, 6), "unit": UNIT,
+                            "sample": f"per step: 10+10 BiCGStab iterations and one force on one field, scaled by "
+                                      f"the calibrated {calib[0]}+{calib[1]} iterations and {w.nrhs} fields"},
+           "e2e": {"value": round(sps, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sf12_nf10")
+    ap.add_argument("--algo", default="mixed_dc", choices=["bicgstab", "mixed_dc", "mixed_dc_half"])
+    ap.add_argument("--maxiter", type=int, default=5000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hbm-case", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 0)
+    rank, world, local_rank = _env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

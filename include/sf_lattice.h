@@ -1,0 +1,191 @@
+/*
+ * sf_lattice.h -- C ABI of the GB300 (sm_103a) library for the fermion part
+ * of the many-flavour HMC molecular-dynamics step of arXiv:1009.5169,
+ * "Improving many flavor QCD simulations using multiple GPUs".
+ *
+ * The calls follow the paper's statement of the problem:
+ *   Eq. (2)  det[D]^{N_f} through N_f/2 additive pseudo-fermions phi_i with
+ *            action S = sum_i |D^{-1} phi_i|^2;
+ *   Alg. 2   blocked force step: solve D X = Phi, then D^dag Y = X, then
+ *            accumulate F_mu = sum_i f[x_i, y_i];
+ *   Eq. (3)  F_mu(n) = sum_i F_{mu,i}(n), f the gauge derivative of
+ *            |D^{-1} phi_i|^2;
+ *   Sec. 3.1 site even/odd preconditioning, Wilson fermions;
+ *   Sec. 3.2 mixed-precision solves (single-precision inner solver inside a
+ *            double-precision outer loop);
+ *   Sec. 4   Schroedinger-functional setup with the SU(3) plaquette action.
+ * D is taken in the hopping-parameter form D = 1 - kappa H,
+ *   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) lambda_mu psi(x+mu)
+ *              + (1 + gamma_mu) U_mu(x-mu)^dag lambda_mu^* psi(x-mu),
+ * with Euclidean chiral gamma matrices (gamma_5 = diag(1,1,-1,-1)), the
+ * fermion on x0 = 1..T-1 (hops leaving that range are dropped), spatial
+ * directions periodic with psi(x + L k) = e^{i theta} psi(x) realised as
+ * lambda_k = e^{i theta/L}, lambda_0 = 1.  The preconditioned operator is
+ * Dhat = 1 - kappa^2 H_eo H_oe on the even sites and det D = det Dhat.
+ *
+ * Layouts (all double precision, complex numbers as (re, im) pairs):
+ *   links   [(T+1) L^3][4][3][3] complex: gauge site lexicographic over
+ *           x0 = 0..T, x1, x2, x3 = 0..L-1 with x3 fastest; mu = 0 is time;
+ *           [a][b] = row a, column b of U_mu(x).  The time link at x0 = T is
+ *           not a link of the SF lattice and is ignored; the spatial links at
+ *           x0 = 0 and x0 = T are the SF boundary fields (they enter only the
+ *           plaquette action).
+ *   even    [nrhs][V/2][4][3] complex, V = L^3 (T-1): the even sites
+ *           ((x0+x1+x2+x3) even) of the fermion lattice in lexicographic
+ *           order (x0 = 1..T-1 slowest, x3 fastest); for even L the site with
+ *           lexicographic index i has even/odd index i/2.  Odd fields alike.
+ *   full    [2][nrhs][V/2][4][3] complex: the even-site block of all fields,
+ *           then the odd-site block.
+ *   force   [(T+1) L^3][4][8]: F^a_mu(x) = dS/d omega^a for
+ *           U_mu(x) -> exp(i omega^a T^a) U_mu(x), T^a = lambda^a / 2 with the
+ *           Gell-Mann matrices; zero on links without fermion support.
+ *
+ * Pointers: every array argument may be a host pointer or a device pointer
+ * of the lattice's device (detected with cudaPointerGetAttributes).  The
+ * caller owns all arrays it passes; the library owns the device copies and
+ * workspaces it allocates.  Device pointers are read and written in order on
+ * the stream given at creation; calls with host pointers return after the
+ * host data is complete.  A lattice object is not thread-safe.
+ *
+ * Errors: no call throws or aborts.  Each returns an sf_status; the message
+ * of the last failure on the calling thread is sf_last_error().  Invalid
+ * sizes or arguments give SF_EINVAL and change nothing; allocation failure
+ * gives SF_ENOMEM; a CUDA failure gives SF_ECUDA.
+ */
+#ifndef SF_LATTICE_H
+#define SF_LATTICE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SF_MAX_RHS 16
+
+typedef struct sf_lattice sf_lattice;
+typedef struct sf_batch sf_batch;
+
+typedef enum {
+    SF_OK = 0,
+    SF_EINVAL = 1,    /* bad argument or size */
+    SF_ENOMEM = 2,    /* device or host allocation failed */
+    SF_ECUDA = 3,     /* a CUDA call failed */
+    SF_ENOCONV = 4,   /* solver stopped above tolerance; outputs hold the best iterate */
+    SF_ETIMEOUT = 5,  /* a bounded device wait ran out */
+    SF_ENOTSU3 = 6    /* a link is not in SU(3) to 1e-12 */
+} sf_status;
+
+typedef enum {
+    SF_OP_DHAT = 0,          /* even -> even: Dhat = 1 - kappa^2 H_eo H_oe */
+    SF_OP_DHAT_DAG = 1,      /* even -> even: Dhat^dag = gamma_5 Dhat gamma_5 */
+    SF_OP_DHATDAG_DHAT = 2,  /* even -> even: Dhat^dag Dhat */
+    SF_OP_D_FULL = 3,        /* full -> full: D = 1 - kappa H */
+    SF_OP_HOP_EO = 4,        /* odd -> even: H_eo */
+    SF_OP_HOP_OE = 5         /* even -> odd: H_oe */
+} sf_op;
+
+typedef enum {
+    SF_FP64 = 0,   /* FP64 storage and arithmetic */
+    SF_FP32 = 1,   /* FP32 storage and arithmetic, links rebuilt from 2 rows */
+    SF_FP16 = 2    /* FP16 operands with a per-(site, rhs) FP32 scale, FP16 links, FP32 arithmetic */
+} sf_prec;
+
+typedef enum {
+    /* BiCGStab in FP64 on all rhs at once, restarted from the true residual
+       until |phi - Dhat x| <= tol |phi| (the plain method, case A of Table 1) */
+    SF_SOLVE_BICGSTAB = 0,
+    /* FP64 defect correction around an FP32 BiCGStab (Sec. 3.2) */
+    SF_SOLVE_MIXED_DC = 1,
+    /* FP64 defect correction around BiCGStab with FP16 hop operands */
+    SF_SOLVE_MIXED_DC_HALF = 2
+} sf_algo;
+
+typedef struct {
+    int iters_outer;                   /* FP64 sweeps of the X solve (max over rhs) */
+    int iters_inner;                   /* inner iterations of the X solve (max over rhs) */
+    int iters_outer_y;                 /* same for the Y solve (0 if Y was not asked for) */
+    int iters_inner_y;
+    int iters_inner_rhs[SF_MAX_RHS];   /* inner iterations of the X solve per rhs */
+    double true_resid[SF_MAX_RHS];     /* |phi_i - Dhat x_i| / |phi_i| (FP64, on the GPU) */
+    double true_resid_y[SF_MAX_RHS];   /* |x_i - Dhat^dag y_i| / |x_i| */
+    double seconds;                    /* host wall time of the call */
+    long long kernel_launches;         /* kernels this call ran on the device */
+} sf_solve_info;
+
+/* Create a lattice of spatial extent L (even, 2..64) and SF time extent T
+ * (2..64), fermion twist theta, hopping parameter kappa and gauge coupling
+ * beta, and upload the gauge field `links` (layout above).  `device` is the
+ * CUDA device ordinal; `stream` a cudaStream_t on that device (NULL: the
+ * legacy default stream).  Returns SF_ENOTSU3 (and no lattice) if a link is
+ * not unitary with unit determinant to 1e-12.  Owns its device memory until
+ * sf_lattice_destroy. */
+sf_status sf_lattice_create(sf_lattice** out, int L, int T, double theta, double kappa, double beta,
+                            const double* links, int device, void* stream);
+
+/* Replace the gauge field (the MD step moves the links) and rebuild the
+ * FP64, FP32 and FP16 link copies the kernels read. */
+sf_status sf_lattice_set_links(sf_lattice* lat, const double* links);
+
+/* Fix the kernel tiling for one precision instead of autotuning it:
+ * TS sites per tile (32, 64 or 128) and NR right-hand sides per thread
+ * (1, 2, 3 or 5; FP64: 1 or 2).  TS = 0 restores autotuning. */
+sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR);
+
+/* Tiling in use for a precision and block size (runs the autotuner if it has
+ * not run yet). */
+sf_status sf_lattice_get_tuning(sf_lattice* lat, sf_prec prec, int nrhs, int* TS, int* NR);
+
+void sf_lattice_destroy(sf_lattice* lat);
+
+/* out = op(in) for nrhs fields (1..SF_MAX_RHS), computed in precision prec
+ * (inputs rounded to it, results returned in FP64).  Even/odd/full layouts
+ * as listed for each op. */
+sf_status wilson_apply_block(sf_lattice* lat, sf_op op, sf_prec prec, int nrhs, const double* in,
+                             double* out);
+
+/* Alg. 2, lines 2-3, on the even sites: X = Dhat^{-1} Phi and, if Y is not
+ * NULL, Y = Dhat^{-dag} X, each to |b - A x| <= tol |b| per right-hand side,
+ * checked on an FP64 recomputation of the residual.  All nrhs systems run
+ * as one block (one launch per kernel for all of them).  maxiter bounds the
+ * inner iterations of each sweep.  On SF_ENOCONV, X and Y hold the best
+ * iterate and info the residuals reached.  info may be NULL. */
+sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* X, double* Y,
+                      double tol, int maxiter, sf_solve_info* info);
+
+/* Eq. (3) with Alg. 2, lines 4-6: the force of S = sum_i |Dhat^{-1} phi_i|^2
+ * from x_i = Dhat^{-1} phi_i and y_i = Dhat^{-dag} x_i (even sites).  Writes
+ * F (force layout, may be NULL) and, if mom is not NULL, does mom -= eps F
+ * in FP64 (mom in the force layout). */
+sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double* Y, double* F, double* mom,
+                        double eps);
+
+/* S_g = beta sum_p w(p) (1 - Re tr U_p / 3) over the SF gauge lattice with
+ * w = 1/2 for spatial plaquettes at x0 = 0 and x0 = T and 1 otherwise. */
+sf_status plaquette_action(sf_lattice* lat, double* S);
+
+/* One launch of the hopping-term kernel H_oe (out_parity 1) or H_eo
+ * (out_parity 0) for nrhs fields in precision prec, on the lattice's
+ * resident operand and result buffers (those wilson_apply_block last packed;
+ * zero after creation), with no packing or unpacking around it.  Enqueued
+ * on the lattice's stream and not synchronised, so a caller can time exactly
+ * one dslash kernel with events on that stream. */
+sf_status wilson_hop_resident(sf_lattice* lat, sf_prec prec, int nrhs, int out_parity);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* sf_last_error(void);
+
+/* ---- batches: several lattices (any sizes) solved by one launch per kernel.
+ * The lattices must live on the same device and stay alive while the batch
+ * exists; their links may change between solves. */
+sf_status sf_batch_create(sf_batch** out, int nlat, sf_lattice* const* lats, int nrhs);
+
+/* solve_block on every lattice of the batch; phi[l], X[l], Y[l] are lattice
+ * l's arrays (Y may be NULL as a whole), info an array of nlat (or NULL). */
+sf_status sf_batch_solve(sf_batch* b, sf_algo algo, const double* const* phi, double* const* X,
+                         double* const* Y, double tol, int maxiter, sf_solve_info* info);
+
+void sf_batch_destroy(sf_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SF_LATTICE_H */

@@ -1,0 +1,1074 @@
+// api.cu -- the C ABI of include/sf_lattice.h: lattice objects, solver
+// workspaces (one lattice or a batch of lattices of any sizes), the tiling
+// autotuner, the graph-captured BiCGStab loop and the FP64 defect-correction
+// driver around it.
+//
+// Solve structure (Alg. 2, lines 2-3; mixed precision as in Sec. 3.2):
+//   x = 0; repeat { r = phi - Dhat x (FP64);  stop if |r| <= tol |phi|;
+//                   solve Dhat e = r/|r| with BiCGStab in the inner precision
+//                   to max(delta_prec, 0.1 tol |phi|/|r|);  x += |r| e }
+// The inner loop is one CUDA graph: a WHILE conditional node whose body holds
+// the seven kernels of one BiCGStab iteration for every right-hand side of
+// every lattice; its last kernel sets the loop condition from the per-rhs
+// convergence flags, so an inner solve costs one graph launch and the host
+// synchronises once per outer sweep.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "sf_kernels.h"
+#include "sf_lattice.h"
+
+using namespace sf;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct SfError {
+    sf_status st;
+    std::string msg;
+};
+
+#define CK(x)                                                                                      \
+    do {                                                                                           \
+        cudaError_t e_ = (x);                                                                      \
+        if (e_ != cudaSuccess)                                                                     \
+            throw SfError{SF_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)};              \
+    } while (0)
+
+#define REQUIRE(cond, msg)                                   \
+    do {                                                     \
+        if (!(cond)) throw SfError{SF_EINVAL, (msg)};        \
+    } while (0)
+
+template <class F>
+sf_status guarded(F&& f) {
+    try {
+        f();
+        return SF_OK;
+    } catch (const SfError& e) {
+        g_err = e.msg;
+        if (e.st == SF_ECUDA) cudaGetLastError();
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        g_err = "host allocation failed";
+        return SF_ENOMEM;
+    } catch (...) {
+        g_err = "unknown error";
+        return SF_ECUDA;
+    }
+}
+
+void* dmalloc(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw SfError{SF_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e)};
+    }
+    return p;
+}
+
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    ~DevMem() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    void ensure(size_t b) {
+        if (b <= bytes) return;
+        release();
+        p = dmalloc(b);
+        bytes = b;
+    }
+    template <class T>
+    T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int prec_index(sf_prec p) { return (int)p; }
+const KrylovOps& ops_for(int ci) {
+    if (ci == 0) return ops_f64();
+    if (ci == 1) return ops_f32();
+    return ops_f32h16();
+}
+Prec vec_prec(int ci) { return ci == 0 ? Prec::F64 : Prec::F32; }
+Prec hop_prec(int ci) { return ci == 0 ? Prec::F64 : ci == 1 ? Prec::F32 : Prec::F16; }
+
+// bytes of a field of S (site, rhs) units
+size_t field_bytes(Prec p, long long S) {
+    if (p == Prec::F64) return (size_t)S * 12 * 16;
+    if (p == Prec::F32) return (size_t)S * 6 * 16;
+    return (size_t)S * 3 * 16;
+}
+
+struct FieldBuf {
+    DevMem v, s;
+    Prec p = Prec::F64;
+    void alloc(Prec pr, long long S) {
+        p = pr;
+        v.ensure(field_bytes(pr, S));
+        CK(cudaMemset(v.p, 0, field_bytes(pr, S)));
+        if (pr == Prec::F16) {
+            s.ensure((size_t)S * sizeof(float));
+            CK(cudaMemset(s.p, 0, (size_t)S * sizeof(float)));
+        }
+    }
+    FieldPtr ptr() const { return FieldPtr{v.p, s.as<float>()}; }
+};
+
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// SF_NO_GRAPH=1 runs the inner BiCGStab loop without the CUDA graph
+bool no_graph() {
+    static const bool v = [] {
+        const char* e = getenv("SF_NO_GRAPH");
+        return e != nullptr && e[0] != '\0' && e[0] != '0';
+    }();
+    return v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- lattice
+struct sf_lattice {
+    int L = 0, T = 0, Vh = 0, Vpad = 0, device = 0, sm_count = 152;
+    double theta = 0, kappa = 0, beta = 0;
+    cudaStream_t stream = nullptr;
+    DevMem canon, u64, u32, u16;
+    DevMem scratch;      // plaquette partials + scalars
+    DevMem stage_in, stage_out;  // device staging for host arrays
+    int tune_TS[3] = {0, 0, 0}, tune_NR[3] = {0, 0, 0};
+    struct Workspace* ws = nullptr;  // own solver workspace (created on first use)
+
+    LatDev base_desc() const {
+        LatDev g;
+        memset(&g, 0, sizeof g);
+        g.L = L;
+        g.T = T;
+        g.Lh = L / 2;
+        g.Vh = Vh;
+        g.Vpad = Vpad;
+        g.L2 = L * L;
+        g.L3 = L * L * L;
+        g.divLh = make_fastdiv((uint32_t)(L / 2));
+        g.divL = make_fastdiv((uint32_t)L);
+        g.kappa = kappa;
+        g.ph_re = cos(theta / L);
+        g.ph_im = sin(theta / L);
+        g.u64 = u64.as<double2>();
+        g.u32 = u32.as<float4>();
+        g.u16 = u16.as<uint2>();
+        return g;
+    }
+    size_t links_bytes() const { return (size_t)(T + 1) * L * L * L * 4 * 18 * sizeof(double); }
+};
+
+// ---------------------------------------------------------------- workspace
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    ~GraphEntry() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+struct Workspace {
+    std::vector<sf_lattice*> lats;
+    int nlat = 0, nrhs = 0, device = 0, sm_count = 152;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    long long S = 0;
+    std::vector<long long> soff;
+
+    struct Cfg {
+        int TS = 0, NR = 0, nblocks = 0;
+        bool ready = false;
+        DevMem lats_dev;
+        std::vector<LatDev> host;
+        LaunchCfg lc{};
+        std::vector<LaunchCfg> per_lat;  // pack / unpack / force on lattice l
+    } cfg[3];
+
+    FieldBuf phi64, x64, y64, r64, t64o, xo64, yo64;
+    struct Inner {
+        FieldBuf x, r, r0, p, v, s, t, tmp, ph, sh;
+        bool ok = false;
+    } inner[3];
+
+    DevMem st, ost, partials, counters, loop_count, nrm_bb, nrm_rr, n_active;
+    DevMem io;  // canonical AoS staging for batched pack/unpack
+    int* pin = nullptr;  // pinned: [0] n_active, [1] loop_count
+    std::map<int, std::unique_ptr<GraphEntry>> graphs;
+    long long launches = 0;
+
+    ~Workspace() {
+        graphs.clear();
+        if (pin) cudaFreeHost(pin);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+
+    void setup(const std::vector<sf_lattice*>& ls, int nr) {
+        lats = ls;
+        nlat = (int)ls.size();
+        nrhs = nr;
+        device = ls[0]->device;
+        sm_count = ls[0]->sm_count;
+        stream = ls[0]->stream;
+        CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+        soff.resize(nlat);
+        S = 0;
+        for (int l = 0; l < nlat; ++l) {
+            soff[l] = S;
+            S += (long long)nrhs * ls[l]->Vpad;
+        }
+        phi64.alloc(Prec::F64, S);
+        x64.alloc(Prec::F64, S);
+        y64.alloc(Prec::F64, S);
+        r64.alloc(Prec::F64, S);
+        t64o.alloc(Prec::F64, S);
+        const size_t n = (size_t)nlat * nrhs;
+        st.ensure(n * sizeof(KState));
+        ost.ensure(n * sizeof(OState));
+        CK(cudaMemset(st.p, 0, n * sizeof(KState)));
+        CK(cudaMemset(ost.p, 0, n * sizeof(OState)));
+        // the most blocks any tiling can use: TS = 32
+        long long maxblk = 0;
+        for (int l = 0; l < nlat; ++l) maxblk += std::min((ls[l]->Vh + 31) / 32, 8 * sm_count);
+        partials.ensure((size_t)3 * nrhs * maxblk * sizeof(double));
+        counters.ensure((size_t)nlat * sizeof(unsigned));
+        CK(cudaMemset(counters.p, 0, (size_t)nlat * sizeof(unsigned)));
+        loop_count.ensure(4 * sizeof(int));  // [0] WHILE iterations, [1] cap, [2] continue flag
+        nrm_bb.ensure(n * sizeof(double));
+        nrm_rr.ensure(n * sizeof(double));
+        n_active.ensure(sizeof(int));
+        CK(cudaHostAlloc(&pin, 8 * sizeof(int), cudaHostAllocDefault));
+    }
+
+    void set_tiling(int ci, int TS, int NR) {
+        Cfg& c = cfg[ci];
+        c.TS = TS;
+        c.NR = NR;
+        c.host.resize(nlat);
+        int blk = 0;
+        for (int l = 0; l < nlat; ++l) {
+            LatDev g = lats[l]->base_desc();
+            g.soff = soff[l];
+            g.ntiles = (g.Vh + TS - 1) / TS;
+            g.nblk = std::min(g.ntiles, 8 * sm_count);
+            g.blk0 = blk;
+            blk += g.nblk;
+            c.host[l] = g;
+        }
+        c.nblocks = blk;
+        c.lats_dev.ensure(sizeof(LatDev) * nlat);
+        CK(cudaMemcpy(c.lats_dev.p, c.host.data(), sizeof(LatDev) * nlat, cudaMemcpyHostToDevice));
+        c.lc = LaunchCfg{c.lats_dev.as<LatDev>(), nlat, nrhs, TS, NR, blk};
+        c.per_lat.resize(nlat);
+        for (int l = 0; l < nlat; ++l) {
+            c.per_lat[l] = LaunchCfg{c.lats_dev.as<LatDev>() + l, 1, nrhs, TS, NR,
+                                     std::max(1, (c.host[l].Vh + 127) / 128)};
+        }
+        c.ready = true;
+        // graphs bake launch shapes in
+        graphs.erase(ci * 2);
+        graphs.erase(ci * 2 + 1);
+    }
+
+    void ensure_inner(int ci) {
+        Inner& in = inner[ci];
+        if (in.ok) return;
+        const Prec pv = vec_prec(ci), ph = hop_prec(ci);
+        in.x.alloc(pv, S);
+        in.r.alloc(pv, S);
+        in.r0.alloc(pv, S);
+        in.p.alloc(pv, S);
+        in.v.alloc(pv, S);
+        in.s.alloc(pv, S);
+        in.t.alloc(pv, S);
+        in.tmp.alloc(ph, S);
+        if (ph != pv) {
+            in.ph.alloc(ph, S);
+            in.sh.alloc(ph, S);
+        }
+        in.ok = true;
+    }
+
+    SolverCtx ctx(bool with_state) {
+        SolverCtx c{};
+        c.st = with_state ? st.as<KState>() : nullptr;
+        c.ost = ost.as<OState>();
+        c.partials = partials.as<double>();
+        c.counters = counters.as<unsigned>();
+        c.loop_count = loop_count.as<int>();
+        c.cond = 0;
+        c.use_cond = 0;
+        return c;
+    }
+
+    FieldPtr hop_in(int ci, const FieldBuf& vec, const FieldBuf& copy) const {
+        return hop_prec(ci) == vec_prec(ci) ? vec.ptr() : copy.ptr();
+    }
+
+    // one BiCGStab iteration on all rhs (7 kernels)
+    void enqueue_iteration(int ci, bool dag, const SolverCtx& k, cudaStream_t s) {
+        const KrylovOps& o = ops_for(ci);
+        const LaunchCfg& lc = cfg[ci].lc;
+        Inner& in = inner[ci];
+        const FieldPtr none{nullptr, nullptr};
+        CK(o.hop(lc, 1, dag, hop_in(ci, in.p, in.ph), in.tmp.ptr(), 1.0, 0, &k, s));
+        CK(o.tail(lc, 0, dag, RED_R0V, in.tmp.ptr(), in.p.ptr(), none, in.v.ptr(), in.r0.ptr(), 1.0, -1.0, 2, &k,
+                  nullptr, s));
+        CK(o.s_update(lc, in.r.ptr(), in.v.ptr(), in.s.ptr(), in.sh.ptr(), &k, s));
+        CK(o.hop(lc, 1, dag, hop_in(ci, in.s, in.sh), in.tmp.ptr(), 1.0, 0, &k, s));
+        CK(o.tail(lc, 0, dag, RED_TS, in.tmp.ptr(), in.s.ptr(), none, in.t.ptr(), none, 1.0, -1.0, 2, &k, nullptr,
+                  s));
+        CK(o.xr_update(lc, in.x.ptr(), in.r.ptr(), in.p.ptr(), in.s.ptr(), in.t.ptr(), in.r0.ptr(), &k, s));
+        CK(o.p_update(lc, in.p.ptr(), in.ph.ptr(), in.r.ptr(), in.v.ptr(), &k, s));
+    }
+
+    GraphEntry& graph(int ci, bool dag) {
+        const int key = ci * 2 + (dag ? 1 : 0);
+        auto it = graphs.find(key);
+        if (it != graphs.end()) return *it->second;
+        auto ge = std::make_unique<GraphEntry>();
+        CK(cudaGraphCreate(&ge->graph, 0));
+        CK(cudaGraphConditionalHandleCreate(&ge->cond, ge->graph, 1, cudaGraphCondAssignDefault));
+        alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+        memset(cp_raw, 0, sizeof cp_raw);
+        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = ge->cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, ge->graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        SolverCtx k = ctx(true);
+        k.cond = ge->cond;
+        k.use_cond = 1;
+        CK(cudaStreamBeginCaptureToGraph(cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        try {
+            enqueue_iteration(ci, dag, k, cap_stream);
+        } catch (...) {
+            cudaGraph_t dummy;
+            cudaStreamEndCapture(cap_stream, &dummy);
+            throw;
+        }
+        CK(cudaStreamEndCapture(cap_stream, &body));
+        CK(cudaGraphInstantiate(&ge->exec, ge->graph, 0));
+        GraphEntry& ref = *ge;
+        graphs[key] = std::move(ge);
+        return ref;
+    }
+
+    // ---- autotuning: time Dhat (hop + fused tail) for each admissible tiling
+    void autotune(int ci);
+
+    void ensure_cfg(int ci) {
+        if (cfg[ci].ready) return;
+        // explicit tiling of the (single) lattice wins
+        if (nlat == 1 && lats[0]->tune_TS[ci] > 0) {
+            set_tiling(ci, lats[0]->tune_TS[ci], lats[0]->tune_NR[ci]);
+            return;
+        }
+        autotune(ci);
+    }
+
+    // FP64: r64 = phi - Dhat x (or Dhat^dag), |r|^2 -> nrm_rr
+    void residual64(bool dag, const FieldBuf& phi, const FieldBuf& x, cudaStream_t s) {
+        ensure_cfg(0);
+        const KrylovOps& o = ops_f64();
+        const LaunchCfg& lc = cfg[0].lc;
+        SolverCtx k = ctx(false);
+        CK(o.hop(lc, 1, dag, x.ptr(), t64o.ptr(), 1.0, 0, nullptr, s));
+        CK(o.tail(lc, 0, dag, RED_NORM, t64o.ptr(), x.ptr(), phi.ptr(), r64.ptr(), FieldPtr{nullptr, nullptr}, -1.0,
+                  1.0, 2, &k, nrm_rr.as<double>(), s));
+        launches += 2;
+    }
+
+    // The full FP64-outer / inner-precision solve of Dhat x = phi (dag: Dhat^dag).
+    // Returns per-rhs (sweeps, inner iterations, true residual).
+    struct Result {
+        std::vector<int> sweeps, inner;
+        std::vector<double> resid;
+        bool converged = true;
+    };
+
+    Result solve(int ci, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
+        ensure_cfg(0);
+        ensure_cfg(ci);
+        ensure_inner(ci);
+        const KrylovOps& o = ops_for(ci);
+        cudaStream_t s = stream;
+        const size_t n = (size_t)nlat * nrhs;
+        const double floor_delta = (ci == 0) ? 0.0 : (ci == 1) ? 1e-5 : 2e-3;
+        const int max_sweeps = (ci == 0) ? 6 : (ci == 1) ? 12 : 24;
+        std::vector<OState> oh(n);
+        for (auto& e : oh) {
+            memset(&e, 0, sizeof e);
+            e.tol2 = tol * tol;
+            e.delta2_floor = floor_delta * floor_delta;
+        }
+        CK(cudaMemcpyAsync(ost.p, oh.data(), n * sizeof(OState), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(x.v.p, 0, field_bytes(Prec::F64, S), s));
+        SolverCtx k0 = ctx(false);
+        CK(launch_norm2(cfg[0].lc, phi.ptr(), &k0, nrm_bb.as<double>(), s));
+        launches += 1;
+        GraphEntry& ge = graph(ci, dag);
+        pin[2] = maxiter + 8;
+        CK(cudaMemcpyAsync(loop_count.as<int>() + 1, pin + 2, sizeof(int), cudaMemcpyHostToDevice, s));
+        SolverCtx k = ctx(true);
+        Result res;
+        for (int sweep = 0;; ++sweep) {
+            if (sweep == 0) {
+                // x = 0: r = phi
+                CK(cudaMemcpyAsync(r64.v.p, phi.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(nrm_rr.p, nrm_bb.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            } else {
+                residual64(dag, phi, x, s);
+            }
+            CK(launch_outer_check((int)n, ost.as<OState>(), nrm_rr.as<double>(),
+                                  sweep == 0 ? nrm_bb.as<double>() : nullptr, max_sweeps, n_active.as<int>(), s));
+            launches += 1;
+            CK(cudaMemcpyAsync(pin, n_active.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (pin[0] == 0) break;
+            CK(o.init(cfg[ci].lc, r64.ptr(), inner[ci].x.ptr(), inner[ci].r.ptr(), inner[ci].r0.ptr(),
+                      inner[ci].p.ptr(), inner[ci].ph.ptr(), &k, maxiter, s));
+            if (no_graph()) {
+                // same kernels launched one by one, the loop condition read back
+                // by the host after each iteration (for profilers that cannot
+                // see inside conditional graph nodes)
+                SolverCtx kn = ctx(true);
+                for (;;) {
+                    enqueue_iteration(ci, dag, kn, s);
+                    CK(cudaMemcpyAsync(pin + 3, loop_count.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+                    CK(cudaStreamSynchronize(s));
+                    if (!pin[3]) break;
+                }
+            } else {
+                CK(cudaGraphLaunch(ge.exec, s));
+            }
+            CK(o.dc_update(cfg[ci].lc, x.ptr(), inner[ci].x.ptr(), &k, s));
+            CK(cudaMemcpyAsync(pin + 1, loop_count.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            launches += 2;
+            CK(cudaStreamSynchronize(s));
+            launches += 7LL * pin[1];
+        }
+        std::vector<OState> out(n);
+        CK(cudaMemcpy(out.data(), ost.p, n * sizeof(OState), cudaMemcpyDeviceToHost));
+        res.sweeps.resize(n);
+        res.inner.resize(n);
+        res.resid.resize(n);
+        for (size_t i = 0; i < n; ++i) {
+            res.sweeps[i] = out[i].sweeps;
+            res.inner[i] = out[i].inner_iters;
+            res.resid[i] = out[i].bb > 0 ? sqrt(out[i].rr / out[i].bb) : 0.0;
+            const bool ok = (out[i].bb == 0.0) || (out[i].rr <= out[i].tol2 * out[i].bb);
+            if (!ok) res.converged = false;
+        }
+        return res;
+    }
+};
+
+namespace {
+
+struct TuneKey {
+    std::vector<std::pair<int, int>> dims;  // (L, T) of each lattice
+    int nrhs, ci, sms;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dims, nrhs, ci, sms) < std::tie(o.dims, o.nrhs, o.ci, o.sms);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+int maxt(int ci, int NR) {
+    if (ci == 0) return NR == 1 ? 256 : 128;
+    return NR == 1 ? 512 : NR == 2 ? 384 : 256;
+}
+
+}  // namespace
+
+void Workspace::autotune(int ci) {
+    TuneKey key;
+    for (auto* l : lats) key.dims.push_back({l->L, l->T});
+    key.nrhs = nrhs;
+    key.ci = ci;
+    key.sms = sm_count;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            set_tiling(ci, it->second.first, it->second.second);
+            return;
+        }
+    }
+    ensure_inner(ci);
+    const KrylovOps& o = ops_for(ci);
+    const int nrs_all[4] = {1, 2, 3, 5};
+    const int tss[3] = {32, 64, 128};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bTS = 64, bNR = 1;
+    const FieldPtr none{nullptr, nullptr};
+    for (int NR : nrs_all) {
+        if (ci == 0 && NR > 2) continue;
+        if (NR > nrhs) continue;
+        const int RG = (nrhs + NR - 1) / NR;
+        for (int TS : tss) {
+            if (TS * RG > maxt(ci, NR)) continue;
+            set_tiling(ci, TS, NR);
+            const LaunchCfg& lc = cfg[ci].lc;
+            Inner& in = inner[ci];
+            auto run = [&]() {
+                CK(o.hop(lc, 1, false, hop_in(ci, in.p, in.ph), in.tmp.ptr(), 1.0, 0, nullptr, stream));
+                CK(o.tail(lc, 0, false, RED_NONE, in.tmp.ptr(), in.p.ptr(), none, in.v.ptr(), none, 1.0, -1.0, 2,
+                          nullptr, nullptr, stream));
+            };
+            run();
+            run();
+            CK(cudaEventRecord(e0, stream));
+            const int reps = 5;
+            for (int r = 0; r < reps; ++r) run();
+            CK(cudaEventRecord(e1, stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bTS = TS;
+                bNR = NR;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_tiling(ci, bTS, bNR);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = {bTS, bNR};
+}
+
+// ---------------------------------------------------------------- helpers
+namespace {
+
+Workspace& lattice_ws(sf_lattice* lat, int nrhs) {
+    if (lat->ws && lat->ws->nrhs == nrhs) return *lat->ws;
+    delete lat->ws;
+    lat->ws = nullptr;
+    auto* w = new Workspace();
+    try {
+        w->setup({lat}, nrhs);
+    } catch (...) {
+        delete w;
+        throw;
+    }
+    lat->ws = w;
+    return *w;
+}
+
+void check_nrhs(int nrhs) { REQUIRE(nrhs >= 1 && nrhs <= SF_MAX_RHS, "nrhs must be in 1..16"); }
+
+// copy a canonical array (host or device) into device memory `dst`
+const double* to_device(const double* src, size_t bytes, DevMem& stage, cudaStream_t s) {
+    if (is_device_ptr(src)) return src;
+    stage.ensure(bytes);
+    CK(cudaMemcpyAsync(stage.p, src, bytes, cudaMemcpyHostToDevice, s));
+    return stage.as<double>();
+}
+
+// where a canonical output goes on the device
+double* out_device(double* dst, size_t bytes, DevMem& stage) {
+    if (is_device_ptr(dst)) return dst;
+    stage.ensure(bytes);
+    return stage.as<double>();
+}
+
+void finish_out(double* dst, const double* dev, size_t bytes, cudaStream_t s) {
+    if (dst != dev) {
+        CK(cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+}
+
+void upload_links(sf_lattice* lat, const double* links) {
+    REQUIRE(links != nullptr, "links is NULL");
+    const size_t bytes = lat->links_bytes();
+    if (is_device_ptr(links)) {
+        CK(cudaMemcpyAsync(lat->canon.p, links, bytes, cudaMemcpyDeviceToDevice, lat->stream));
+    } else {
+        CK(cudaMemcpyAsync(lat->canon.p, links, bytes, cudaMemcpyHostToDevice, lat->stream));
+    }
+    // SU(3) check
+    unsigned long long* err = reinterpret_cast<unsigned long long*>(lat->scratch.as<char>());
+    CK(launch_su3_check(lat->L, lat->T, lat->canon.as<double>(), err, lat->stream));
+    unsigned long long h[2];
+    CK(cudaMemcpyAsync(h, err, sizeof h, cudaMemcpyDeviceToHost, lat->stream));
+    CK(cudaStreamSynchronize(lat->stream));
+    double e1, e2;
+    memcpy(&e1, &h[0], 8);
+    memcpy(&e2, &h[1], 8);
+    if (!(e1 <= 1e-12) || !(e2 <= 1e-12)) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "links not in SU(3): max|U^dag U - 1| = %.3e, max|det U - 1| = %.3e", e1, e2);
+        throw SfError{SF_ENOTSU3, buf};
+    }
+    const LatDev g = lat->base_desc();
+    CK(launch_link_prep(g, lat->canon.as<double>(), lat->u64.as<double2>(), lat->u32.as<float4>(),
+                        lat->u16.as<uint2>(), lat->stream));
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* sf_last_error(void) { return g_err.c_str(); }
+
+sf_status sf_lattice_create(sf_lattice** out, int L, int T, double theta, double kappa, double beta,
+                            const double* links, int device, void* stream) {
+    return guarded([&] {
+        REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        REQUIRE(L >= 2 && L <= 64 && (L % 2) == 0, "L must be even and in 2..64");
+        REQUIRE(T >= 2 && T <= 64, "T must be in 2..64");
+        REQUIRE(std::isfinite(theta) && std::isfinite(kappa) && std::isfinite(beta), "non-finite parameter");
+        int ndev = 0;
+        CK(cudaGetDeviceCount(&ndev));
+        REQUIRE(device >= 0 && device < ndev, "bad device ordinal");
+        CK(cudaSetDevice(device));
+        std::unique_ptr<sf_lattice> lat(new sf_lattice());
+        lat->L = L;
+        lat->T = T;
+        lat->theta = theta;
+        lat->kappa = kappa;
+        lat->beta = beta;
+        lat->device = device;
+        lat->stream = reinterpret_cast<cudaStream_t>(stream);
+        CK(cudaDeviceGetAttribute(&lat->sm_count, cudaDevAttrMultiProcessorCount, device));
+        lat->Vh = L * L * L * (T - 1) / 2;
+        lat->Vpad = round_up(lat->Vh, 64);
+        lat->canon.ensure(lat->links_bytes());
+        lat->u64.ensure((size_t)4 * 2 * 9 * lat->Vpad * sizeof(double2));
+        lat->u32.ensure((size_t)4 * 2 * 3 * lat->Vpad * sizeof(float4));
+        lat->u16.ensure((size_t)4 * 2 * 3 * lat->Vpad * sizeof(uint2));
+        lat->scratch.ensure(4096 + 2048 * sizeof(double));
+        CK(cudaMemset(lat->scratch.p, 0, lat->scratch.bytes));
+        upload_links(lat.get(), links);
+        *out = lat.release();
+    });
+}
+
+sf_status sf_lattice_set_links(sf_lattice* lat, const double* links) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr, "lattice is NULL");
+        CK(cudaSetDevice(lat->device));
+        upload_links(lat, links);
+    });
+}
+
+sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr, "lattice is NULL");
+        REQUIRE(prec >= SF_FP64 && prec <= SF_FP16, "bad precision");
+        const int ci = prec_index(prec);
+        if (TS != 0) {
+            REQUIRE(TS == 32 || TS == 64 || TS == 128, "TS must be 32, 64 or 128");
+            REQUIRE(NR == 1 || NR == 2 || NR == 3 || NR == 5, "NR must be 1, 2, 3 or 5");
+            REQUIRE(!(ci == 0 && NR > 2), "FP64 supports NR = 1 or 2");
+        }
+        lat->tune_TS[ci] = TS;
+        lat->tune_NR[ci] = NR;
+        if (lat->ws) lat->ws->cfg[ci].ready = false;
+    });
+}
+
+sf_status sf_lattice_get_tuning(sf_lattice* lat, sf_prec prec, int nrhs, int* TS, int* NR) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr && TS != nullptr && NR != nullptr, "NULL argument");
+        REQUIRE(prec >= SF_FP64 && prec <= SF_FP16, "bad precision");
+        check_nrhs(nrhs);
+        CK(cudaSetDevice(lat->device));
+        Workspace& w = lattice_ws(lat, nrhs);
+        const int ci = prec_index(prec);
+        w.ensure_cfg(ci);
+        *TS = w.cfg[ci].TS;
+        *NR = w.cfg[ci].NR;
+    });
+}
+
+void sf_lattice_destroy(sf_lattice* lat) {
+    if (!lat) return;
+    cudaSetDevice(lat->device);
+    if (lat->stream) cudaStreamSynchronize(lat->stream);
+    delete lat->ws;
+    delete lat;
+}
+
+sf_status wilson_apply_block(sf_lattice* lat, sf_op op, sf_prec prec, int nrhs, const double* in, double* out) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr && in != nullptr && out != nullptr, "NULL argument");
+        REQUIRE(op >= SF_OP_DHAT && op <= SF_OP_HOP_OE, "bad op");
+        REQUIRE(prec >= SF_FP64 && prec <= SF_FP16, "bad precision");
+        check_nrhs(nrhs);
+        CK(cudaSetDevice(lat->device));
+        Workspace& w = lattice_ws(lat, nrhs);
+        const int ci = prec_index(prec);
+        w.ensure_cfg(ci);
+        w.ensure_inner(ci);
+        const KrylovOps& o = ops_for(ci);
+        const LaunchCfg& lc = w.cfg[ci].lc;
+        const LaunchCfg& pl = w.cfg[ci].per_lat[0];
+        cudaStream_t s = lat->stream;
+        const size_t half = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
+        const bool full = (op == SF_OP_D_FULL);
+        const size_t in_bytes = full ? 2 * half : half, out_bytes = full ? 2 * half : half;
+        const double* din = to_device(in, in_bytes, lat->stage_in, s);
+        double* dout = out_device(out, out_bytes, lat->stage_out);
+        Workspace::Inner& I = w.inner[ci];
+        const FieldPtr none{nullptr, nullptr};
+        const bool split = hop_prec(ci) != vec_prec(ci);
+        // A = vector-precision copy of the input, Ah = hop-precision copy
+        FieldBuf& A = I.x;
+        FieldBuf& Ah = split ? I.ph : I.x;
+        FieldBuf& B = I.r;   // odd half of a full input
+        FieldBuf& Bh = split ? I.sh : I.r;
+        auto pack_both = [&](const double* src, FieldBuf& v, FieldBuf& h) {
+            CK(o.pack(pl, src, v.ptr(), s));
+            if (split) CK(o.pack_h(pl, src, h.ptr(), s));
+        };
+        switch (op) {
+            case SF_OP_HOP_EO:
+            case SF_OP_HOP_OE: {
+                pack_both(din, A, Ah);
+                CK(o.hop(lc, op == SF_OP_HOP_EO ? 0 : 1, false, Ah.ptr(), I.tmp.ptr(), 1.0, 0, nullptr, s));
+                CK(o.unpack_h(pl, I.tmp.ptr(), dout, s));
+                break;
+            }
+            case SF_OP_DHAT:
+            case SF_OP_DHAT_DAG:
+            case SF_OP_DHATDAG_DHAT: {
+                pack_both(din, A, Ah);
+                const bool d1 = (op == SF_OP_DHAT_DAG);
+                CK(o.hop(lc, 1, d1, Ah.ptr(), I.tmp.ptr(), 1.0, 0, nullptr, s));
+                CK(o.tail(lc, 0, d1, RED_NONE, I.tmp.ptr(), A.ptr(), none, I.v.ptr(), none, 1.0, -1.0, 2, nullptr,
+                          nullptr, s));
+                FieldBuf* res = &I.v;
+                if (op == SF_OP_DHATDAG_DHAT) {
+                    // second application needs the hop-precision copy of the intermediate
+                    if (split) {
+                        CK(o.unpack(pl, I.v.ptr(), dout, s));
+                        CK(o.pack_h(pl, dout, I.sh.ptr(), s));
+                    }
+                    CK(o.hop(lc, 1, true, split ? I.sh.ptr() : I.v.ptr(), I.tmp.ptr(), 1.0, 0, nullptr, s));
+                    CK(o.tail(lc, 0, true, RED_NONE, I.tmp.ptr(), I.v.ptr(), none, I.t.ptr(), none, 1.0, -1.0, 2,
+                              nullptr, nullptr, s));
+                    res = &I.t;
+                }
+                CK(o.unpack(pl, res->ptr(), dout, s));
+                break;
+            }
+            case SF_OP_D_FULL: {
+                const double* de = din;
+                const double* dod = din + (size_t)nrhs * lat->Vh * 24;
+                pack_both(de, A, Ah);
+                pack_both(dod, B, Bh);
+                // even: in_e - kappa H_eo in_o ; odd: in_o - kappa H_oe in_e
+                CK(o.tail(lc, 0, false, RED_NONE, Bh.ptr(), A.ptr(), none, I.v.ptr(), none, 1.0, -1.0, 1, nullptr,
+                          nullptr, s));
+                CK(o.tail(lc, 1, false, RED_NONE, Ah.ptr(), B.ptr(), none, I.t.ptr(), none, 1.0, -1.0, 1, nullptr,
+                          nullptr, s));
+                CK(o.unpack(pl, I.v.ptr(), dout, s));
+                CK(o.unpack(pl, I.t.ptr(), dout + (size_t)nrhs * lat->Vh * 24, s));
+                break;
+            }
+        }
+        finish_out(out, dout, out_bytes, s);
+        CK(cudaGetLastError());
+    });
+}
+
+sf_status wilson_hop_resident(sf_lattice* lat, sf_prec prec, int nrhs, int out_parity) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr, "lattice is NULL");
+        REQUIRE(prec >= SF_FP64 && prec <= SF_FP16, "bad precision");
+        REQUIRE(out_parity == 0 || out_parity == 1, "out_parity must be 0 or 1");
+        check_nrhs(nrhs);
+        CK(cudaSetDevice(lat->device));
+        Workspace& w = lattice_ws(lat, nrhs);
+        const int ci = prec_index(prec);
+        w.ensure_cfg(ci);
+        w.ensure_inner(ci);
+        Workspace::Inner& I = w.inner[ci];
+        const bool split = hop_prec(ci) != vec_prec(ci);
+        CK(ops_for(ci).hop(w.cfg[ci].lc, out_parity, false, split ? I.ph.ptr() : I.x.ptr(), I.tmp.ptr(), 1.0, 0,
+                           nullptr, lat->stream));
+    });
+}
+
+namespace {
+
+void fill_info(sf_solve_info* info, const Workspace::Result& rx, const Workspace::Result* ry, int l, int nrhs,
+               double secs, long long launches) {
+    if (!info) return;
+    memset(info, 0, sizeof *info);
+    for (int i = 0; i < nrhs; ++i) {
+        const int k = l * nrhs + i;
+        info->iters_outer = std::max(info->iters_outer, rx.sweeps[k]);
+        info->iters_inner = std::max(info->iters_inner, rx.inner[k]);
+        info->iters_inner_rhs[i] = rx.inner[k];
+        info->true_resid[i] = rx.resid[k];
+        if (ry) {
+            info->iters_outer_y = std::max(info->iters_outer_y, ry->sweeps[k]);
+            info->iters_inner_y = std::max(info->iters_inner_y, ry->inner[k]);
+            info->true_resid_y[i] = ry->resid[k];
+        }
+    }
+    info->seconds = secs;
+    info->kernel_launches = launches;
+}
+
+int algo_index(sf_algo a) {
+    switch (a) {
+        case SF_SOLVE_BICGSTAB: return 0;
+        case SF_SOLVE_MIXED_DC: return 1;
+        case SF_SOLVE_MIXED_DC_HALF: return 2;
+    }
+    throw SfError{SF_EINVAL, "bad algorithm"};
+}
+
+}  // namespace
+
+sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* X, double* Y, double tol,
+                      int maxiter, sf_solve_info* info) {
+    bool noconv = false;
+    sf_status st = guarded([&] {
+        const auto t0 = std::chrono::steady_clock::now();
+        REQUIRE(lat != nullptr && phi != nullptr && X != nullptr, "NULL argument");
+        check_nrhs(nrhs);
+        REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
+        REQUIRE(maxiter >= 1, "maxiter must be >= 1");
+        const int ci = algo_index(algo);
+        CK(cudaSetDevice(lat->device));
+        Workspace& w = lattice_ws(lat, nrhs);
+        w.launches = 0;
+        w.ensure_cfg(0);
+        w.ensure_cfg(ci);
+        cudaStream_t s = lat->stream;
+        const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
+        const LaunchCfg& pl = w.cfg[0].per_lat[0];
+        const double* dphi = to_device(phi, bytes, lat->stage_in, s);
+        CK(ops_f64().pack(pl, dphi, w.phi64.ptr(), s));
+        w.launches += 1;
+        Workspace::Result rx = w.solve(ci, false, w.phi64, w.x64, tol, maxiter);
+        double* dX = out_device(X, bytes, lat->stage_out);
+        CK(ops_f64().unpack(pl, w.x64.ptr(), dX, s));
+        w.launches += 1;
+        finish_out(X, dX, bytes, s);
+        Workspace::Result ry;
+        bool have_y = false;
+        if (Y) {
+            ry = w.solve(ci, true, w.x64, w.y64, tol, maxiter);
+            have_y = true;
+            double* dY = out_device(Y, bytes, lat->stage_out);
+            CK(ops_f64().unpack(pl, w.y64.ptr(), dY, s));
+            w.launches += 1;
+            finish_out(Y, dY, bytes, s);
+        }
+        CK(cudaStreamSynchronize(s));
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        fill_info(info, rx, have_y ? &ry : nullptr, 0, nrhs, secs, w.launches);
+        if (!rx.converged || (have_y && !ry.converged)) noconv = true;
+    });
+    if (st == SF_OK && noconv) {
+        g_err = "solver stopped above tolerance";
+        return SF_ENOCONV;
+    }
+    return st;
+}
+
+sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double* Y, double* F, double* mom,
+                        double eps) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr && X != nullptr && Y != nullptr, "NULL argument");
+        REQUIRE(F != nullptr || mom != nullptr, "F and mom are both NULL");
+        check_nrhs(nrhs);
+        CK(cudaSetDevice(lat->device));
+        Workspace& w = lattice_ws(lat, nrhs);
+        w.ensure_cfg(0);
+        if (!w.xo64.v.p) {
+            w.xo64.alloc(Prec::F64, w.S);
+            w.yo64.alloc(Prec::F64, w.S);
+        }
+        cudaStream_t s = lat->stream;
+        const KrylovOps& o = ops_f64();
+        const LaunchCfg& lc = w.cfg[0].lc;
+        const LaunchCfg& pl = w.cfg[0].per_lat[0];
+        const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
+        const double* dX = to_device(X, bytes, lat->stage_in, s);
+        CK(o.pack(pl, dX, w.x64.ptr(), s));
+        const double* dY = to_device(Y, bytes, lat->stage_in, s);
+        CK(o.pack(pl, dY, w.y64.ptr(), s));
+        // odd-site reconstruction: Xh_o = kappa H_oe x_e, Yh_o = kappa gamma_5 H_oe gamma_5 y_e
+        CK(o.hop(lc, 1, false, w.x64.ptr(), w.xo64.ptr(), 1.0, 1, nullptr, s));
+        CK(o.hop(lc, 1, true, w.y64.ptr(), w.yo64.ptr(), 1.0, 1, nullptr, s));
+        const size_t fbytes = (size_t)(lat->T + 1) * lat->L * lat->L * lat->L * 4 * 8 * sizeof(double);
+        double* dF = nullptr;
+        if (F) {
+            dF = out_device(F, fbytes, lat->stage_out);
+            CK(cudaMemsetAsync(dF, 0, fbytes, s));
+        }
+        double* dM = nullptr;
+        DevMem mstage;
+        if (mom) {
+            if (is_device_ptr(mom)) {
+                dM = mom;
+            } else {
+                mstage.ensure(fbytes);
+                CK(cudaMemcpyAsync(mstage.p, mom, fbytes, cudaMemcpyHostToDevice, s));
+                dM = mstage.as<double>();
+            }
+        }
+        CK(launch_force(pl, w.x64.ptr(), w.xo64.ptr(), w.y64.ptr(), w.yo64.ptr(), dF, dM, eps, s));
+        if (F) finish_out(F, dF, fbytes, s);
+        if (mom && dM != mom) {
+            CK(cudaMemcpyAsync(mom, dM, fbytes, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        CK(cudaGetLastError());
+    });
+}
+
+sf_status plaquette_action(sf_lattice* lat, double* S) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr && S != nullptr, "NULL argument");
+        CK(cudaSetDevice(lat->device));
+        char* base = lat->scratch.as<char>();
+        unsigned* counter = reinterpret_cast<unsigned*>(base + 64);
+        double* out = reinterpret_cast<double*>(base + 128);
+        double* partials = reinterpret_cast<double*>(base + 4096);
+        CK(launch_plaquette(lat->L, lat->T, lat->beta, lat->canon.as<double>(), partials, counter, out,
+                            lat->stream));
+        double h = 0;
+        CK(cudaMemcpyAsync(&h, out, sizeof h, cudaMemcpyDeviceToHost, lat->stream));
+        CK(cudaStreamSynchronize(lat->stream));
+        *S = h;
+    });
+}
+
+// ---------------------------------------------------------------- batches
+}  // extern "C"
+
+struct sf_batch {
+    Workspace ws;
+};
+
+extern "C" {
+
+sf_status sf_batch_create(sf_batch** out, int nlat, sf_lattice* const* lats, int nrhs) {
+    return guarded([&] {
+        REQUIRE(out != nullptr && lats != nullptr, "NULL argument");
+        *out = nullptr;
+        REQUIRE(nlat >= 1 && nlat <= 4096, "nlat must be in 1..4096");
+        check_nrhs(nrhs);
+        std::vector<sf_lattice*> v(lats, lats + nlat);
+        for (auto* l : v) {
+            REQUIRE(l != nullptr, "NULL lattice");
+            REQUIRE(l->device == v[0]->device, "lattices on different devices");
+        }
+        CK(cudaSetDevice(v[0]->device));
+        std::unique_ptr<sf_batch> b(new sf_batch());
+        b->ws.setup(v, nrhs);
+        *out = b.release();
+    });
+}
+
+sf_status sf_batch_solve(sf_batch* b, sf_algo algo, const double* const* phi, double* const* X, double* const* Y,
+                         double tol, int maxiter, sf_solve_info* info) {
+    bool noconv = false;
+    sf_status st = guarded([&] {
+        const auto t0 = std::chrono::steady_clock::now();
+        REQUIRE(b != nullptr && phi != nullptr && X != nullptr, "NULL argument");
+        REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
+        REQUIRE(maxiter >= 1, "maxiter must be >= 1");
+        Workspace& w = b->ws;
+        const int ci = algo_index(algo);
+        CK(cudaSetDevice(w.device));
+        w.launches = 0;
+        w.ensure_cfg(0);
+        w.ensure_cfg(ci);
+        cudaStream_t s = w.stream;
+        for (int l = 0; l < w.nlat; ++l) {
+            REQUIRE(phi[l] != nullptr && X[l] != nullptr, "NULL array in batch");
+            const size_t bytes = (size_t)w.nrhs * w.lats[l]->Vh * 24 * sizeof(double);
+            const double* d = to_device(phi[l], bytes, w.io, s);
+            CK(ops_f64().pack(w.cfg[0].per_lat[l], d, w.phi64.ptr(), s));
+            if (d != phi[l]) CK(cudaStreamSynchronize(s));
+            w.launches += 1;
+        }
+        Workspace::Result rx = w.solve(ci, false, w.phi64, w.x64, tol, maxiter);
+        Workspace::Result ry;
+        if (Y) ry = w.solve(ci, true, w.x64, w.y64, tol, maxiter);
+        for (int l = 0; l < w.nlat; ++l) {
+            const size_t bytes = (size_t)w.nrhs * w.lats[l]->Vh * 24 * sizeof(double);
+            double* dX = out_device(X[l], bytes, w.io);
+            CK(ops_f64().unpack(w.cfg[0].per_lat[l], w.x64.ptr(), dX, s));
+            finish_out(X[l], dX, bytes, s);
+            if (Y && Y[l]) {
+                double* dY = out_device(Y[l], bytes, w.io);
+                CK(ops_f64().unpack(w.cfg[0].per_lat[l], w.y64.ptr(), dY, s));
+                finish_out(Y[l], dY, bytes, s);
+            }
+        }
+        CK(cudaStreamSynchronize(s));
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (info)
+            for (int l = 0; l < w.nlat; ++l) fill_info(info + l, rx, Y ? &ry : nullptr, l, w.nrhs, secs, w.launches);
+        if (!rx.converged || (Y && !ry.converged)) noconv = true;
+    });
+    if (st == SF_OK && noconv) {
+        g_err = "solver stopped above tolerance";
+        return SF_ENOCONV;
+    }
+    return st;
+}
+
+void sf_batch_destroy(sf_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->ws.device);
+    if (b->ws.stream) cudaStreamSynchronize(b->ws.stream);
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,788 @@
+// krylov_impl.cuh -- the Wilson hop, the fused Dhat tail and the BiCGStab
+// step kernels, templated over field storage.  Included by one translation
+// unit per precision configuration (krylov_f64.cu, krylov_f32.cu,
+// krylov_f16.cu), each of which instantiates one KrylovOps table.
+//
+// Operator (hopping-parameter form of the Wilson operator with the
+// Schroedinger-functional boundaries used by the paper's SF runs, Sec. 4):
+//   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) lambda_mu psi(x+mu)
+//              + (1 + gamma_mu) U_mu(x-mu)^dag lambda_mu^* psi(x-mu),
+//   lambda_0 = 1, lambda_k = e^{i theta/L}; time hops leaving x0 = 1..T-1 are
+//   dropped (Dirichlet).  Even/odd preconditioning (Sec. 3.1):
+//   Dhat = 1 - kappa^2 H_eo H_oe,  Dhat^dag = gamma_5 Dhat gamma_5, where
+//   gamma_5 H gamma_5 swaps the projectors (1 -+ gamma_mu).
+// Each block owns a lattice's tiles of TS sites x (nrhs / NR) groups of NR
+// right-hand sides; a thread loads a link once and applies it to its NR
+// right-hand sides.  Reductions are deterministic: a fixed shuffle tree per
+// warp, a fixed sum over warps, and the lattice's last block sums the
+// per-block partials in block order.
+#pragma once
+#include <type_traits>
+
+#include "sf_kernels.h"
+
+namespace sf {
+
+template <typename P> struct LinkOf;
+template <> struct LinkOf<P64> { static __device__ __forceinline__ const double2* ptr(const LatDev& g) { return g.u64; } };
+template <> struct LinkOf<P32> { static __device__ __forceinline__ const float4* ptr(const LatDev& g) { return g.u32; } };
+template <> struct LinkOf<P16> { static __device__ __forceinline__ const uint2* ptr(const LatDev& g) { return g.u16; } };
+
+template <typename P> __host__ __device__ __forceinline__ CField<P> cf(FieldPtr f) {
+    return CField<P>{reinterpret_cast<const typename P::vec*>(f.v), f.s};
+}
+template <typename P> __host__ __device__ __forceinline__ Field<P> wf(FieldPtr f) {
+    return Field<P>{reinterpret_cast<typename P::vec*>(f.v), f.s};
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// element offsets of (lattice block, rhs)
+template <typename P>
+__device__ __forceinline__ long long vbase(const LatDev& g, int rhs) {
+    return (g.soff + (long long)rhs * g.Vpad) * P::NC;
+}
+__device__ __forceinline__ long long sbase(const LatDev& g, int rhs) { return g.soff + (long long)rhs * g.Vpad; }
+
+// Threads per block a kernel of a (precision, NR) configuration may be
+// launched with; it sets the register budget 65536 / MAXT per thread.
+template <typename P, int NR>
+struct KB {
+    static constexpr int MAXT = std::is_same<P, P64>::value ? (NR == 1 ? 256 : 128)
+                                                           : (NR == 1 ? 512 : NR == 2 ? 384 : 256);
+};
+
+// ------------------------------------------------------------ hop
+template <int MU, typename P, int NR, bool DAG>
+__device__ __forceinline__ void hop_dir(const LatDev& g, const SiteX& s, int cb, int out_par,
+                                        const CField<P>& in, int r0, int nval,
+                                        cpx<typename P::real> (&acc)[NR][4][3]) {
+    using R = typename P::real;
+    constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma_mu
+    constexpr int SB = -SF;
+    const cpx<R> ph = cpx<R>{(R)g.ph_re, (R)g.ph_im};
+    if (MU != 0 || s.x0 < g.T - 1) {
+        const int ncb = neighbour_cb<MU, +1>(g, s);
+        Link<R> U;
+        load_link(g, LinkOf<P>::ptr(g), MU, out_par, cb, U);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j < nval) {
+                cpx<R> p[4][3];
+                load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
+                cpx<R> h[2][3], w[2][3];
+                project<MU, SF>(p, h);
+                if (MU != 0) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) h[k][a] = ph * h[k][a];
+                }
+                mul_link(U, h, w);
+                expand_add<MU, SF>(acc[j], w);
+            }
+        }
+    }
+    if (MU != 0 || s.x0 > 1) {
+        const int ncb = neighbour_cb<MU, -1>(g, s);
+        Link<R> U;
+        load_link(g, LinkOf<P>::ptr(g), MU, out_par ^ 1, ncb, U);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j < nval) {
+                cpx<R> p[4][3];
+                load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
+                cpx<R> h[2][3], w[2][3];
+                project<MU, SB>(p, h);
+                if (MU != 0) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) h[k][a] = conj(ph) * h[k][a];
+                }
+                mul_link_dag(U, h, w);
+                expand_add<MU, SB>(acc[j], w);
+            }
+        }
+    }
+}
+
+template <typename P, int NR, bool DAG>
+__device__ __forceinline__ void hop_site(const LatDev& g, const SiteX& s, int cb, int out_par,
+                                         const CField<P>& in, int r0, int nval,
+                                         cpx<typename P::real> (&acc)[NR][4][3]) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[j][sp][a] = cpx<typename P::real>{0, 0};
+    hop_dir<0, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    hop_dir<1, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    hop_dir<2, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    hop_dir<3, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+}
+
+// ------------------------------------------------------------ reductions
+constexpr int MAX_WARPS = 32;
+constexpr int MAX_RHS = 16;
+
+// Block-reduce vals[j][q] (rhs = threadIdx.y * NR + j), publish per-block
+// partials, and in the lattice's last block sum them in block order into
+// sres[rhs * NQ + q].  Returns true in that last block.  Every thread of the
+// block must call it.
+template <int NR, int NQ>
+__device__ bool reduce_lattice(const double (&vals)[NR][NQ], int nrhs, int l, const LatDev& g,
+                               double* __restrict__ partials, unsigned* __restrict__ counters, double* sres) {
+    __shared__ double sw[MAX_WARPS][NR][NQ];
+    __shared__ int is_last;
+    const int lane = threadIdx.x & 31;
+    const int wpr = blockDim.x >> 5;
+    const int w = threadIdx.y * wpr + (threadIdx.x >> 5);
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double v = vals[j][q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) sw[w][j][q] = v;
+        }
+    __syncthreads();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < (int)blockDim.y * NR * NQ) {
+        const int y = tid / (NR * NQ), jq = tid % (NR * NQ), j = jq / NQ, q = jq % NQ;
+        const int rhs = y * NR + j;
+        if (rhs < nrhs) {
+            double s = 0.0;
+            for (int k = 0; k < wpr; ++k) s += sw[y * wpr + k][j][q];
+            partials[(long long)(rhs * NQ + q) * gridDim.x + blockIdx.x] = s;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned prev = atomicAdd(&counters[l], 1u);
+        is_last = (prev == (unsigned)(g.nblk - 1));
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    const int nw = (int)(blockDim.x * blockDim.y) >> 5;
+    for (int pr = tid >> 5; pr < nrhs * NQ; pr += nw) {
+        double s = 0.0;
+        for (int b = lane; b < g.nblk; b += 32) s += __ldcg(partials + (long long)pr * gridDim.x + g.blk0 + b);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) sres[pr] = s;
+    }
+    __syncthreads();
+    if (tid == 0) counters[l] = 0u;
+    return true;
+}
+
+template <typename R>
+__device__ __forceinline__ void dotc_acc(const cpx<R> (&a)[4][3], const cpx<R> (&b)[4][3], double& re, double& im) {
+    R sr = 0, si = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sr = fma(a[s][c].re, b[s][c].re, sr);
+            sr = fma(a[s][c].im, b[s][c].im, sr);
+            si = fma(a[s][c].re, b[s][c].im, si);
+            si = fma(-a[s][c].im, b[s][c].re, si);
+        }
+    re += (double)sr;
+    im += (double)si;
+}
+template <typename R>
+__device__ __forceinline__ void norm_acc(const cpx<R> (&a)[4][3], double& n) {
+    R s = 0;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            s = fma(a[sp][c].re, a[sp][c].re, s);
+            s = fma(a[sp][c].im, a[sp][c].im, s);
+        }
+    n += (double)s;
+}
+
+__device__ __forceinline__ bool rhs_active(const KState* st, int idx) { return st == nullptr || st[idx].active != 0; }
+
+// ------------------------------------------------------------ kernels
+// out(out_par) = coef * H in
+template <typename PI, typename PO, int NR, bool DAG>
+__global__ void __launch_bounds__(KB<PI, NR>::MAXT) k_hop(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
+                                              CField<PI> in, Field<PO> out, double coef, int kpow,
+                                              const KState* __restrict__ st) {
+    using R = typename PI::real;
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y * NR;
+    const int nval = min(NR, nrhs - r0);
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+        if (j < nval && rhs_active(st, l * nrhs + r0 + j)) any = true;
+    if (!any) return;
+    const R c = (R)(coef * (kpow == 0 ? 1.0 : kpow == 1 ? g.kappa : g.kappa * g.kappa));
+    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
+        const int cb = tile * blockDim.x + threadIdx.x;
+        if (cb >= g.Vh) break;
+        const SiteX s = decode_site(g, cb, out_par);
+        cpx<R> acc[NR][4][3];
+        hop_site<PI, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j < nval) {
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) acc[j][sp][a] = c * acc[j][sp][a];
+                store_spinor<PO, R>(out, vbase<PO>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), acc[j]);
+            }
+        }
+    }
+}
+
+// out(out_par) = a * xv + coef * H hin (+ zv) with a fused reduction
+template <typename PH, typename PV, int NR, bool DAG, int RED, bool HASZ>
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_tail(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
+                                               CField<PH> hin, CField<PV> xv, CField<PV> zv, Field<PV> out,
+                                               CField<PV> ra, double a, double coef, int kpow,
+                                               SolverCtx ctx, double* __restrict__ norm_out) {
+    using RH = typename PH::real;
+    using RV = typename PV::real;
+    constexpr int NQ = (RED == RED_TS) ? 3 : (RED == RED_R0V) ? 2 : 1;
+    __shared__ double sres[MAX_RHS * 3];
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y * NR;
+    const int nval = min(NR, nrhs - r0);
+    bool act[NR];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        act[j] = (j < nval) && rhs_active(ctx.st, l * nrhs + r0 + j);
+        any = any || act[j];
+    }
+    double red[NR][NQ];
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) red[j][q] = 0.0;
+    const RV av = (RV)a;
+    const RV cv = (RV)(coef * (kpow == 0 ? 1.0 : kpow == 1 ? g.kappa : g.kappa * g.kappa));
+    if (any) {
+        for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
+            const int cb = tile * blockDim.x + threadIdx.x;
+            if (cb >= g.Vh) break;
+            const SiteX s = decode_site(g, cb, out_par);
+            cpx<RH> acc[NR][4][3];
+            hop_site<PH, NR, DAG>(g, s, cb, out_par, hin, r0, nval, acc);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                if (!act[j]) continue;
+                cpx<RV> x[4][3], o[4][3];
+                load_spinor<PV, RV>(xv, vbase<PV>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), x);
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        o[sp][c] = cpx<RV>{av * x[sp][c].re + cv * (RV)acc[j][sp][c].re,
+                                           av * x[sp][c].im + cv * (RV)acc[j][sp][c].im};
+                if (HASZ) {
+                    cpx<RV> z[4][3];
+                    load_spinor<PV, RV>(zv, vbase<PV>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), z);
+#pragma unroll
+                    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) o[sp][c] = o[sp][c] + z[sp][c];
+                }
+                store_spinor<PV, RV>(out, vbase<PV>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), o);
+                if (RED == RED_R0V) {
+                    cpx<RV> q0[4][3];
+                    load_spinor<PV, RV>(ra, vbase<PV>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), q0);
+                    dotc_acc(q0, o, red[j][0], red[j][NQ > 1 ? 1 : 0]);
+                } else if (RED == RED_TS) {
+                    dotc_acc(o, x, red[j][0], red[j][NQ > 1 ? 1 : 0]);
+                    norm_acc(o, red[j][NQ > 2 ? 2 : 0]);
+                } else if (RED == RED_NORM) {
+                    norm_acc(o, red[j][0]);
+                }
+            }
+        }
+    }
+    if (RED == RED_NONE) return;
+    if (!reduce_lattice<NR, NQ>(red, nrhs, l, g, ctx.partials, ctx.counters, sres)) return;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < nrhs) {
+        const int i = l * nrhs + tid;
+        if (RED == RED_NORM) {
+            norm_out[i] = sres[tid];
+        } else if (ctx.st != nullptr && ctx.st[i].active) {
+            KState& st = ctx.st[i];
+            if (RED == RED_R0V) {
+                const double2 r0v = make_double2(sres[tid * NQ], sres[tid * NQ + (NQ > 1 ? 1 : 0)]);
+                if (r0v.x == 0.0 && r0v.y == 0.0) {
+                    st.active = 0;
+                    st.flags |= 1;
+                } else {
+                    st.alpha = cdiv(st.rho, r0v);
+                }
+            } else if (RED == RED_TS) {
+                const double2 ts = make_double2(sres[tid * NQ], sres[tid * NQ + (NQ > 1 ? 1 : 0)]);
+                const double tt = sres[tid * NQ + (NQ > 2 ? 2 : 0)];
+                if (tt > 0.0) {
+                    st.omega = make_double2(ts.x / tt, ts.y / tt);
+                } else {
+                    st.omega = make_double2(0.0, 0.0);
+                }
+            }
+        }
+    }
+}
+
+// s = r - alpha v (and its hop-precision copy)
+template <typename PV, typename PH, int NR>
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_s_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                   CField<PV> r, CField<PV> v, Field<PV> s, Field<PH> sh,
+                                                   const KState* __restrict__ st) {
+    using RV = typename PV::real;
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y * NR;
+    const int nval = min(NR, nrhs - r0);
+    constexpr bool COPY = !std::is_same<PV, PH>::value;
+    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
+        const int cb = tile * blockDim.x + threadIdx.x;
+        if (cb >= g.Vh) break;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j >= nval) continue;
+            const KState& k = st[l * nrhs + r0 + j];
+            if (!k.active) continue;
+            const cpx<RV> al = cpx<RV>{(RV)k.alpha.x, (RV)k.alpha.y};
+            cpx<RV> a[4][3], b[4][3];
+            load_spinor<PV, RV>(r, vbase<PV>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), a);
+            load_spinor<PV, RV>(v, vbase<PV>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), b);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) a[sp][c] = a[sp][c] - al * b[sp][c];
+            store_spinor<PV, RV>(s, vbase<PV>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), a);
+            if (COPY) store_spinor<PH, RV>(sh, vbase<PH>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), a);
+        }
+    }
+}
+
+// x += alpha p + omega s ; r = s - omega t ; rho' = <r0, r>, rr = |r|^2
+template <typename PV, int NR>
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_xr_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                    Field<PV> x, Field<PV> r, CField<PV> p, CField<PV> s,
+                                                    CField<PV> t, CField<PV> r0f, SolverCtx ctx) {
+    using RV = typename PV::real;
+    __shared__ double sres[MAX_RHS * 3];
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y * NR;
+    const int nval = min(NR, nrhs - r0);
+    double red[NR][3];
+    bool act[NR];
+    cpx<RV> al[NR], om[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        red[j][0] = red[j][1] = red[j][2] = 0.0;
+        act[j] = (j < nval) && ctx.st[l * nrhs + r0 + j].active;
+        if (act[j]) {
+            const KState& k = ctx.st[l * nrhs + r0 + j];
+            al[j] = cpx<RV>{(RV)k.alpha.x, (RV)k.alpha.y};
+            om[j] = cpx<RV>{(RV)k.omega.x, (RV)k.omega.y};
+        }
+    }
+    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
+        const int cb = tile * blockDim.x + threadIdx.x;
+        if (cb >= g.Vh) break;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (!act[j]) continue;
+            const long long vb = vbase<PV>(g, r0 + j), sb = sbase(g, r0 + j);
+            cpx<RV> xa[4][3], pa[4][3], sa[4][3], ta[4][3];
+            load_spinor<PV, RV>(CField<PV>{x.v, x.scale}, vb, g.Vpad, cb, sb, xa);
+            load_spinor<PV, RV>(p, vb, g.Vpad, cb, sb, pa);
+            load_spinor<PV, RV>(s, vb, g.Vpad, cb, sb, sa);
+            load_spinor<PV, RV>(t, vb, g.Vpad, cb, sb, ta);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    xa[sp][c] = xa[sp][c] + al[j] * pa[sp][c] + om[j] * sa[sp][c];
+                    sa[sp][c] = sa[sp][c] - om[j] * ta[sp][c];
+                }
+            store_spinor<PV, RV>(x, vb, g.Vpad, cb, sb, xa);
+            store_spinor<PV, RV>(r, vb, g.Vpad, cb, sb, sa);
+            cpx<RV> q0[4][3];
+            load_spinor<PV, RV>(r0f, vb, g.Vpad, cb, sb, q0);
+            dotc_acc(q0, sa, red[j][0], red[j][1]);
+            norm_acc(sa, red[j][2]);
+        }
+    }
+    if (!reduce_lattice<NR, 3>(red, nrhs, l, g, ctx.partials, ctx.counters, sres)) return;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < nrhs) {
+        KState& st = ctx.st[l * nrhs + tid];
+        if (st.active) {
+            const double2 rho_new = make_double2(sres[tid * 3], sres[tid * 3 + 1]);
+            const double rr = sres[tid * 3 + 2];
+            st.rr = rr;
+            st.iters += 1;
+            const bool om0 = (st.omega.x == 0.0 && st.omega.y == 0.0);
+            const bool rho0 = (rho_new.x == 0.0 && rho_new.y == 0.0);
+            if (!om0 && !rho0) st.beta = cmul(cdiv(rho_new, st.rho), cdiv(st.alpha, st.omega));
+            st.rho = rho_new;
+            if (om0) st.flags |= 2;
+            if (rho0) st.flags |= 1;
+            const bool go = (rr > st.target2) && (st.iters < st.maxiter) && !om0 && !rho0;
+            st.active = go ? 1 : 0;
+        }
+    }
+}
+
+// p = r + beta (p - omega v); the first block also drives the WHILE node
+template <typename PV, typename PH, int NR>
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_p_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                   Field<PV> p, Field<PH> ph, CField<PV> r, CField<PV> v,
+                                                   SolverCtx ctx) {
+    using RV = typename PV::real;
+    constexpr bool COPY = !std::is_same<PV, PH>::value;
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y * NR;
+    const int nval = min(NR, nrhs - r0);
+    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
+        const int cb = tile * blockDim.x + threadIdx.x;
+        if (cb >= g.Vh) break;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j >= nval) continue;
+            const KState& k = ctx.st[l * nrhs + r0 + j];
+            if (!k.active) continue;
+            const cpx<RV> be = cpx<RV>{(RV)k.beta.x, (RV)k.beta.y};
+            const cpx<RV> om = cpx<RV>{(RV)k.omega.x, (RV)k.omega.y};
+            const long long vb = vbase<PV>(g, r0 + j), sb = sbase(g, r0 + j);
+            cpx<RV> pa[4][3], ra[4][3], va[4][3];
+            load_spinor<PV, RV>(CField<PV>{p.v, p.scale}, vb, g.Vpad, cb, sb, pa);
+            load_spinor<PV, RV>(r, vb, g.Vpad, cb, sb, ra);
+            load_spinor<PV, RV>(v, vb, g.Vpad, cb, sb, va);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) pa[sp][c] = ra[sp][c] + be * (pa[sp][c] - om * va[sp][c]);
+            store_spinor<PV, RV>(p, vb, g.Vpad, cb, sb, pa);
+            if (COPY) store_spinor<PH, RV>(ph, vbase<PH>(g, r0 + j), g.Vpad, cb, sb, pa);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        int any = 0;
+        for (int i = 0; i < nlat * nrhs; ++i) any |= ctx.st[i].active;
+        const int n = atomicAdd(ctx.loop_count, 1) + 1;
+        const int go = (any && n < ctx.loop_count[1]) ? 1 : 0;
+        ctx.loop_count[2] = go;  // read by the host when the loop runs without a graph
+        if (ctx.use_cond) cudaGraphSetConditional(ctx.cond, (unsigned)go);
+    }
+}
+
+// inner start: b = r64 / |r64|; x = 0, r = r0 = p = b
+template <typename PV, typename PH, int NR>
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_inner_init(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                     CField<P64> r64, Field<PV> x, Field<PV> r, Field<PV> r0f,
+                                                     Field<PV> p, Field<PH> ph, SolverCtx ctx, int maxiter) {
+    using RV = typename PV::real;
+    constexpr bool COPY = !std::is_same<PV, PH>::value;
+    __shared__ double sres[MAX_RHS * 3];
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y * NR;
+    const int nval = min(NR, nrhs - r0);
+    double red[NR][1];
+    bool act[NR];
+    double inv[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        red[j][0] = 0.0;
+        act[j] = (j < nval) && ctx.ost[l * nrhs + r0 + j].active;
+        inv[j] = act[j] ? ctx.ost[l * nrhs + r0 + j].inv_norm : 0.0;
+    }
+    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
+        const int cb = tile * blockDim.x + threadIdx.x;
+        if (cb >= g.Vh) break;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (!act[j]) continue;
+            const long long sb = sbase(g, r0 + j);
+            cpx<double> b64[4][3];
+            load_spinor<P64, double>(r64, vbase<P64>(g, r0 + j), g.Vpad, cb, sb, b64);
+            cpx<RV> b[4][3], z[4][3];
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    b[sp][c] = cpx<RV>{(RV)(b64[sp][c].re * inv[j]), (RV)(b64[sp][c].im * inv[j])};
+                    z[sp][c] = cpx<RV>{(RV)0, (RV)0};
+                }
+            const long long vb = vbase<PV>(g, r0 + j);
+            store_spinor<PV, RV>(x, vb, g.Vpad, cb, sb, z);
+            store_spinor<PV, RV>(r, vb, g.Vpad, cb, sb, b);
+            store_spinor<PV, RV>(r0f, vb, g.Vpad, cb, sb, b);
+            store_spinor<PV, RV>(p, vb, g.Vpad, cb, sb, b);
+            if (COPY) store_spinor<PH, RV>(ph, vbase<PH>(g, r0 + j), g.Vpad, cb, sb, b);
+            norm_acc(b, red[j][0]);
+        }
+    }
+    if (!reduce_lattice<NR, 1>(red, nrhs, l, g, ctx.partials, ctx.counters, sres)) return;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < nrhs) {
+        const int i = l * nrhs + tid;
+        KState& st = ctx.st[i];
+        const OState& o = ctx.ost[i];
+        st.rho = make_double2(sres[tid], 0.0);
+        st.rr = sres[tid];
+        st.alpha = make_double2(1.0, 0.0);
+        st.omega = make_double2(1.0, 0.0);
+        st.beta = make_double2(0.0, 0.0);
+        st.iters = 0;
+        st.maxiter = maxiter;
+        st.flags = 0;
+        st.target2 = o.delta2;
+        st.active = (o.active && sres[tid] > o.delta2) ? 1 : 0;
+    }
+    if (tid == 0) *ctx.loop_count = 0;
+}
+
+// x64 += x / inv_norm for the rhs that iterated in this sweep
+template <typename PV, int NR>
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_dc_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                    Field<P64> x64, CField<PV> x, SolverCtx ctx) {
+    using RV = typename PV::real;
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y * NR;
+    const int nval = min(NR, nrhs - r0);
+    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
+        const int cb = tile * blockDim.x + threadIdx.x;
+        if (cb >= g.Vh) break;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j >= nval) continue;
+            const OState& o = ctx.ost[l * nrhs + r0 + j];
+            if (!o.active) continue;
+            const double sc = 1.0 / o.inv_norm;
+            const long long sb = sbase(g, r0 + j);
+            cpx<RV> e[4][3];
+            cpx<double> xa[4][3];
+            load_spinor<PV, RV>(x, vbase<PV>(g, r0 + j), g.Vpad, cb, sb, e);
+            load_spinor<P64, double>(CField<P64>{x64.v, nullptr}, vbase<P64>(g, r0 + j), g.Vpad, cb, sb, xa);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    xa[sp][c].re += sc * (double)e[sp][c].re;
+                    xa[sp][c].im += sc * (double)e[sp][c].im;
+                }
+            store_spinor<P64, double>(x64, vbase<P64>(g, r0 + j), g.Vpad, cb, sb, xa);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        for (int i = 0; i < nlat * nrhs; ++i)
+            if (ctx.ost[i].active) {
+                ctx.ost[i].sweeps += 1;
+                ctx.ost[i].inner_iters += ctx.st[i].iters;
+            }
+    }
+}
+
+// canonical AoS FP64 [rhs][Vh][12 complex] of one lattice <-> field
+template <typename P>
+__global__ void k_pack(const LatDev* __restrict__ lat, int nrhs, const double* __restrict__ aos, Field<P> out) {
+    using R = typename P::real;
+    const LatDev g = *lat;
+    const int rhs = blockIdx.y;
+    for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.Vh; cb += gridDim.x * blockDim.x) {
+        const double2* src = reinterpret_cast<const double2*>(aos) + ((long long)rhs * g.Vh + cb) * 12;
+        cpx<R> p[4][3];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const double2 v = src[c];
+            p[c / 3][c % 3] = cpx<R>{(R)v.x, (R)v.y};
+        }
+        store_spinor<P, R>(out, vbase<P>(g, rhs), g.Vpad, cb, sbase(g, rhs), p);
+    }
+}
+
+template <typename P>
+__global__ void k_unpack(const LatDev* __restrict__ lat, int nrhs, CField<P> in, double* __restrict__ aos) {
+    using R = typename P::real;
+    const LatDev g = *lat;
+    const int rhs = blockIdx.y;
+    for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.Vh; cb += gridDim.x * blockDim.x) {
+        cpx<R> p[4][3];
+        load_spinor<P, R>(in, vbase<P>(g, rhs), g.Vpad, cb, sbase(g, rhs), p);
+        double2* dst = reinterpret_cast<double2*>(aos) + ((long long)rhs * g.Vh + cb) * 12;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) dst[c] = make_double2((double)p[c / 3][c % 3].re, (double)p[c / 3][c % 3].im);
+    }
+}
+
+// ------------------------------------------------------------ launchers
+inline dim3 block_of(const LaunchCfg& c) { return dim3(c.TS, (c.nrhs + c.NR - 1) / c.NR); }
+
+// RHS block widths compiled per precision: FP64 keeps to 1 and 2 (wider
+// blocks spill; the FP64 hop is bound by the FP64 pipe, not by link reuse).
+#define SF_NR_SWITCH(NRV, ...)                                                    \
+    switch (NRV) {                                                                \
+        case 1: { constexpr int NR_ = 1; __VA_ARGS__; break; }                    \
+        case 2: { constexpr int NR_ = 2; __VA_ARGS__; break; }                    \
+        case 3: { if constexpr (!std::is_same<PV, P64>::value) { constexpr int NR_ = 3; __VA_ARGS__; } else return cudaErrorInvalidValue; break; } \
+        case 5: { if constexpr (!std::is_same<PV, P64>::value) { constexpr int NR_ = 5; __VA_ARGS__; } else return cudaErrorInvalidValue; break; } \
+        default: return cudaErrorInvalidValue;                                    \
+    }
+
+template <typename PV, typename PH>
+struct OpsImpl {
+    static cudaError_t hop(const LaunchCfg& c, int out_par, bool dag, FieldPtr in, FieldPtr out, double coef,
+                           int kpow, const SolverCtx* ctx, cudaStream_t st) {
+        const KState* ks = ctx ? ctx->st : nullptr;
+        SF_NR_SWITCH(c.NR, {
+            if (dag)
+                k_hop<PH, PH, NR_, true><<<c.nblocks, block_of(c), 0, st>>>(
+                    c.lats, c.nlat, c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
+            else
+                k_hop<PH, PH, NR_, false><<<c.nblocks, block_of(c), 0, st>>>(
+                    c.lats, c.nlat, c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
+        });
+        return cudaGetLastError();
+    }
+
+    template <int NR, bool DAG>
+    static void tail_red(const LaunchCfg& c, int out_par, int red, FieldPtr hin, FieldPtr xv, FieldPtr zv,
+                         FieldPtr out, FieldPtr ra, double a, double coef, int kpow, SolverCtx k,
+                         double* norm_out, cudaStream_t st) {
+        const dim3 b = block_of(c);
+        const bool hz = zv.v != nullptr;
+#define SF_TAIL(RED, HZ)                                                                              \
+    k_tail<PH, PV, NR, DAG, RED, HZ><<<c.nblocks, b, 0, st>>>(c.lats, c.nlat, c.nrhs, out_par, cf<PH>(hin), \
+                                                              cf<PV>(xv), cf<PV>(zv), wf<PV>(out), cf<PV>(ra), \
+                                                              a, coef, kpow, k, norm_out)
+        switch (red) {
+            case RED_NONE: if (hz) SF_TAIL(RED_NONE, true); else SF_TAIL(RED_NONE, false); break;
+            case RED_R0V: SF_TAIL(RED_R0V, false); break;
+            case RED_TS: SF_TAIL(RED_TS, false); break;
+            case RED_NORM: if (hz) SF_TAIL(RED_NORM, true); else SF_TAIL(RED_NORM, false); break;
+        }
+#undef SF_TAIL
+    }
+
+    static cudaError_t tail(const LaunchCfg& c, int out_par, bool dag, int red, FieldPtr hin, FieldPtr xv,
+                            FieldPtr zv, FieldPtr out, FieldPtr ra, double a, double coef, int kpow,
+                            const SolverCtx* ctx, double* norm_out, cudaStream_t st) {
+        SolverCtx k{};
+        if (ctx) k = *ctx;
+        SF_NR_SWITCH(c.NR, {
+            if (dag) tail_red<NR_, true>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+            else tail_red<NR_, false>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+        });
+        return cudaGetLastError();
+    }
+
+    static cudaError_t init(const LaunchCfg& c, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
+                            FieldPtr ph, const SolverCtx* ctx, int maxiter, cudaStream_t st) {
+        SF_NR_SWITCH(c.NR, {
+            k_inner_init<PV, PH, NR_><<<c.nblocks, block_of(c), 0, st>>>(
+                c.lats, c.nlat, c.nrhs, cf<P64>(r64), wf<PV>(x), wf<PV>(r), wf<PV>(r0), wf<PV>(p), wf<PH>(ph),
+                *ctx, maxiter);
+        });
+        return cudaGetLastError();
+    }
+
+    static cudaError_t s_update(const LaunchCfg& c, FieldPtr r, FieldPtr v, FieldPtr s, FieldPtr sh,
+                                const SolverCtx* ctx, cudaStream_t st) {
+        SF_NR_SWITCH(c.NR, {
+            k_s_update<PV, PH, NR_><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<PV>(r),
+                                                                        cf<PV>(v), wf<PV>(s), wf<PH>(sh), ctx->st);
+        });
+        return cudaGetLastError();
+    }
+
+    static cudaError_t xr_update(const LaunchCfg& c, FieldPtr x, FieldPtr r, FieldPtr p, FieldPtr s, FieldPtr t,
+                                 FieldPtr r0, const SolverCtx* ctx, cudaStream_t st) {
+        SF_NR_SWITCH(c.NR, {
+            k_xr_update<PV, NR_><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, wf<PV>(x), wf<PV>(r),
+                                                                     cf<PV>(p), cf<PV>(s), cf<PV>(t), cf<PV>(r0),
+                                                                     *ctx);
+        });
+        return cudaGetLastError();
+    }
+
+    static cudaError_t p_update(const LaunchCfg& c, FieldPtr p, FieldPtr ph, FieldPtr r, FieldPtr v,
+                                const SolverCtx* ctx, cudaStream_t st) {
+        SF_NR_SWITCH(c.NR, {
+            k_p_update<PV, PH, NR_><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, wf<PV>(p),
+                                                                        wf<PH>(ph), cf<PV>(r), cf<PV>(v), *ctx);
+        });
+        return cudaGetLastError();
+    }
+
+    static cudaError_t dc_update(const LaunchCfg& c, FieldPtr x64, FieldPtr x, const SolverCtx* ctx,
+                                 cudaStream_t st) {
+        SF_NR_SWITCH(c.NR, {
+            k_dc_update<PV, NR_><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, wf<P64>(x64),
+                                                                     cf<PV>(x), *ctx);
+        });
+        return cudaGetLastError();
+    }
+
+    static cudaError_t pack(const LaunchCfg& c, const double* aos, FieldPtr out, cudaStream_t st) {
+        k_pack<PV><<<dim3(64, c.nrhs), 256, 0, st>>>(c.lats, c.nrhs, aos, wf<PV>(out));
+        return cudaGetLastError();
+    }
+    static cudaError_t unpack(const LaunchCfg& c, FieldPtr in, double* aos, cudaStream_t st) {
+        k_unpack<PV><<<dim3(64, c.nrhs), 256, 0, st>>>(c.lats, c.nrhs, cf<PV>(in), aos);
+        return cudaGetLastError();
+    }
+    static cudaError_t pack_h(const LaunchCfg& c, const double* aos, FieldPtr out, cudaStream_t st) {
+        k_pack<PH><<<dim3(64, c.nrhs), 256, 0, st>>>(c.lats, c.nrhs, aos, wf<PH>(out));
+        return cudaGetLastError();
+    }
+    static cudaError_t unpack_h(const LaunchCfg& c, FieldPtr in, double* aos, cudaStream_t st) {
+        k_unpack<PH><<<dim3(64, c.nrhs), 256, 0, st>>>(c.lats, c.nrhs, cf<PH>(in), aos);
+        return cudaGetLastError();
+    }
+
+    static KrylovOps table(Prec pv, Prec ph) {
+        KrylovOps o;
+        o.pv = pv;
+        o.ph = ph;
+        o.hop = &hop;
+        o.tail = &tail;
+        o.init = &init;
+        o.s_update = &s_update;
+        o.xr_update = &xr_update;
+        o.p_update = &p_update;
+        o.dc_update = &dc_update;
+        o.pack = &pack;
+        o.unpack = &unpack;
+        o.pack_h = &pack_h;
+        o.unpack_h = &unpack_h;
+        return o;
+    }
+};
+
+}  // namespace sf

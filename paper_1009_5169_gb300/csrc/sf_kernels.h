@@ -1,0 +1,119 @@
+// sf_kernels.h -- host-side launch interface of the sm_103a kernels.
+// Each precision configuration (field storage of the Krylov vectors, PV, and
+// of the hop operands, PH) is compiled in its own translation unit and
+// exposes one table of launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sf_device.cuh"
+
+namespace sf {
+
+enum class Prec : int { F64 = 0, F32 = 1, F16 = 2 };
+
+// reductions fused into the tail of a D-hat application
+enum Red : int { RED_NONE = 0, RED_R0V = 1, RED_TS = 2, RED_NORM = 3 };
+
+// Per (lattice, rhs) state of one BiCGStab iteration, in device memory.
+struct KState {
+    double2 rho, alpha, omega, beta;
+    double rr;        // |r|^2 of the iterated residual
+    double target2;   // iterate while rr > target2
+    int active;       // 1 while this rhs iterates
+    int iters;        // iterations done in this inner solve
+    int maxiter;      // inner cap
+    int flags;        // bit 0: breakdown (rho or <r0,v> = 0), bit 1: omega = 0
+};
+
+// Per (lattice, rhs) state of the FP64 defect-correction loop.
+struct OState {
+    double bb;        // |phi|^2
+    double rr;        // |phi - Dhat x|^2 of the last true residual
+    double tol2;      // stop when rr <= tol2 * bb
+    double delta2_floor;  // inner relative target (squared) the precision can reach
+    double delta2;    // inner relative target (squared) of the current sweep
+    double inv_norm;  // 1 / |r| used to normalise the inner right-hand side
+    int active;       // still above tolerance
+    int sweeps;
+    int inner_iters;  // cumulative inner iterations
+    int pad_;
+};
+
+struct LaunchCfg {
+    const LatDev* lats;   // device array
+    int nlat;
+    int nrhs;
+    int TS;               // sites per tile (multiple of 32)
+    int NR;               // right-hand sides per thread (1, 2, 3 or 5)
+    int nblocks;          // total blocks (sum of lattice nblk)
+};
+
+struct SolverCtx {
+    KState* st;           // [nlat * nrhs]
+    OState* ost;          // [nlat * nrhs]
+    double* partials;     // [NQmax * nrhs * nblocks]
+    unsigned* counters;   // [nlat], self-resetting
+    int* loop_count;      // [0] iterations of the WHILE loop, [1] their cap, [2] continue flag
+    cudaGraphConditionalHandle cond;
+    int use_cond;
+};
+
+// Untyped field handle: planes plus (FP16 only) the per-site scales.
+struct FieldPtr {
+    void* v;
+    float* s;
+};
+
+struct KrylovOps {
+    Prec pv, ph;
+    // out(parity) = coef kappa_l^kpow H in  (hop operands, PH storage);
+    // with ctx, right-hand sides whose KState is inactive are skipped
+    cudaError_t (*hop)(const LaunchCfg&, int out_par, bool dag, FieldPtr in, FieldPtr out, double coef, int kpow,
+                       const SolverCtx*, cudaStream_t);
+    // out = a xv + coef kappa_l^kpow H hin (+ zv) with an optional fused reduction
+    cudaError_t (*tail)(const LaunchCfg&, int out_par, bool dag, int red, FieldPtr hin, FieldPtr xv,
+                        FieldPtr zv, FieldPtr out, FieldPtr ra, double a, double coef, int kpow,
+                        const SolverCtx*, double* norm_out, cudaStream_t);
+    // inner init from the FP64 residual r64
+    cudaError_t (*init)(const LaunchCfg&, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
+                        FieldPtr ph, const SolverCtx*, int maxiter, cudaStream_t);
+    cudaError_t (*s_update)(const LaunchCfg&, FieldPtr r, FieldPtr v, FieldPtr s, FieldPtr sh,
+                            const SolverCtx*, cudaStream_t);
+    cudaError_t (*xr_update)(const LaunchCfg&, FieldPtr x, FieldPtr r, FieldPtr p, FieldPtr s, FieldPtr t,
+                             FieldPtr r0, const SolverCtx*, cudaStream_t);
+    cudaError_t (*p_update)(const LaunchCfg&, FieldPtr p, FieldPtr ph, FieldPtr r, FieldPtr v,
+                            const SolverCtx*, cudaStream_t);
+    // x64 += x / inv_norm for outer-active rhs
+    cudaError_t (*dc_update)(const LaunchCfg&, FieldPtr x64, FieldPtr x, const SolverCtx*, cudaStream_t);
+    // canonical AoS FP64 [lattice block][rhs][Vh][12 complex] <-> this precision
+    cudaError_t (*pack)(const LaunchCfg&, const double* aos, FieldPtr out, cudaStream_t);
+    cudaError_t (*unpack)(const LaunchCfg&, FieldPtr in, double* aos, cudaStream_t);
+    // the same for the hop-operand storage PH
+    cudaError_t (*pack_h)(const LaunchCfg&, const double* aos, FieldPtr out, cudaStream_t);
+    cudaError_t (*unpack_h)(const LaunchCfg&, FieldPtr in, double* aos, cudaStream_t);
+};
+
+const KrylovOps& ops_f64();
+const KrylovOps& ops_f32();
+const KrylovOps& ops_f32h16();
+
+// FP64 defect-correction control: sets OState.active / inv_norm from the
+// residual norms; writes the number of active rhs to *n_active.
+cudaError_t launch_outer_check(int n, OState* ost, const double* rr, const double* bb_or_null, int max_sweeps,
+                               int* n_active, cudaStream_t);
+// |f|^2 per (lattice, rhs) of an FP64 field
+cudaError_t launch_norm2(const LaunchCfg&, FieldPtr f64, const SolverCtx*, double* out, cudaStream_t);
+
+// link preparation: canonical AoS FP64 gauge field -> kernel layouts
+cudaError_t launch_link_prep(const LatDev& g, const double* canon, double2* u64, float4* u32, uint2* u16,
+                             cudaStream_t);
+// max |U^dag U - 1| and max |det U - 1| over the gauge field's links
+cudaError_t launch_su3_check(int L, int T, const double* canon, unsigned long long* out2, cudaStream_t);
+cudaError_t launch_plaquette(int L, int T, double beta, const double* canon, double* partials,
+                             unsigned* counter, double* out, cudaStream_t);
+// force from the full-lattice FP64 fields Xh = (x_e, x_o), Yh = (y_e, y_o)
+cudaError_t launch_force(const LaunchCfg&, FieldPtr xe, FieldPtr xo, FieldPtr ye, FieldPtr yo, double* F,
+                         double* mom, double eps, cudaStream_t);
+
+}  // namespace sf

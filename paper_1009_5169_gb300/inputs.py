@@ -27,8 +27,8 @@ Random numbers come from numpy's counter-based Philox generator keyed by
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
-from typing import List, Optional
+from dataclasses import dataclass
+from typing import List
 
 import numpy as np
 
@@ -63,11 +63,26 @@ def half_volume(L: int, T: int) -> int:
     return V // 2
 
 
-def _expi_hermitian(H: np.ndarray, eps: float) -> np.ndarray:
-    """exp(i eps H) for a batch of Hermitian matrices via eigendecomposition."""
+def _expi_hermitian(H: np.ndarray, eps: float, device=None) -> np.ndarray:
+    """exp(i eps H) for a batch of Hermitian matrices via eigendecomposition.
+
+    With ``device`` (a torch CUDA device) the eigendecomposition runs there,
+    which is much faster for large gauge fields; the Gaussian draws are the
+    same, the result differs only by rounding."""
+    if device is not None:
+        import torch
+        flat = H.reshape(-1, 3, 3)
+        out = np.empty_like(flat)
+        chunk = 1 << 16   # the batched solver's workspace grows with the batch
+        for a in range(0, flat.shape[0], chunk):
+            Ht = torch.from_numpy(flat[a:a + chunk]).to(device)
+            w, V = torch.linalg.eigh(Ht)
+            ph = torch.exp(1j * eps * w.to(torch.complex128))
+            out[a:a + chunk] = ((V * ph[..., None, :]) @ V.conj().transpose(-1, -2)).cpu().numpy()
+        return out.reshape(H.shape)
     w, V = np.linalg.eigh(H)
     ph = np.exp(1j * eps * w)
-    return np.einsum("...ab,...b,...cb->...ac", V, ph, V.conj())
+    return (V * ph[..., None, :]) @ np.swapaxes(V.conj(), -1, -2)
 
 
 def gaussian_traceless_hermitian(g: np.random.Generator, shape) -> np.ndarray:
@@ -78,14 +93,14 @@ def gaussian_traceless_hermitian(g: np.random.Generator, shape) -> np.ndarray:
     return H
 
 
-def links(L: int, T: int, eps: float, seed: int, field_id: int = FIELD_LINKS) -> np.ndarray:
+def links(L: int, T: int, eps: float, seed: int, field_id: int = FIELD_LINKS, device=None) -> np.ndarray:
     """SF gauge field U = exp(i eps H), shape [(T+1) L^3, 4, 3, 3] complex128."""
     if L % 2 or L < 2 or T < 2:
         raise ValueError("need even L >= 2 and T >= 2")
     g = rng(seed, field_id)
     n = gauge_sites(L, T)
     H = gaussian_traceless_hermitian(g, (n, 4))
-    U = _expi_hermitian(H, eps)
+    U = _expi_hermitian(H, eps, device)
     U = U.reshape(T + 1, L ** 3, 4, 3, 3)
     eye = np.eye(3, dtype=np.complex128)
     U[0, :, 1:] = eye          # boundary spatial links at x0 = 0

@@ -1,0 +1,256 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances: FP64 operator and force results 1e-12 relative (max-abs error
+over max-abs value); solutions are judged by the oracle's own FP64 true
+residual |b - A x| / |b| <= the requested tolerance; FP32 / FP16 operator
+results by their storage precision (relative 2e-6 / 4e-3).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1009_5169_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sf():
+    from paper_1009_5169_gb300 import binding, build
+    build.build()
+    return binding
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+CASES = [
+    # L, T, eps, kappa, theta, nrhs  (ragged tails: Vh not a multiple of any tile)
+    (4, 4, 0.3, 0.125, 0.5, 1),
+    (6, 5, 0.4, 0.13, 0.5, 3),
+    (8, 8, 0.3, 0.125, 0.5, 5),
+    (4, 9, 0.25, 0.12, 1.1, 2),
+]
+
+
+def _lattice(sf, L, T, eps, kappa, theta, seed=1234, device_links=True):
+    U = inputs.links(L, T, eps, seed)
+    Ud = torch.from_numpy(U).cuda() if device_links else U
+    return U, sf.Lattice(L, T, theta, kappa, 4.52, Ud)
+
+
+@pytest.mark.parametrize("L,T,eps,kappa,theta,nrhs", CASES)
+def test_apply_fp64_matches_oracle(sf, L, T, eps, kappa, theta, nrhs):
+    U, lat = _lattice(sf, L, T, eps, kappa, theta)
+    x = inputs.sources(L, T, nrhs, 99)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    for op, dag in (("dhat", False), ("dhat_dag", True)):
+        sf.wilson_apply_block(lat, op, "fp64", xd, out)
+        ref = oracle.apply_dhat(U, x, L, T, theta, kappa, dagger=dag)
+        assert relerr(out.cpu().numpy(), ref) <= 1e-12, op
+    sf.wilson_apply_block(lat, "dhatdag_dhat", "fp64", xd, out)
+    ref = oracle.apply_dhat(U, oracle.apply_dhat(U, x, L, T, theta, kappa), L, T, theta, kappa, dagger=True)
+    assert relerr(out.cpu().numpy(), ref) <= 1e-12
+    # hops and the full operator
+    full = inputs.full_sources(L, T, nrhs, 98)
+    fe, fo = oracle.split_eo(full, L, T)
+    Hf = oracle.hop(U, full, L, T, theta)
+    He, Ho = oracle.split_eo(Hf, L, T)
+    Hx_oe = oracle.split_eo(oracle.hop(U, oracle.join_eo(fe, 0 * fo, L, T), L, T, theta), L, T)[1]
+    Hx_eo = oracle.split_eo(oracle.hop(U, oracle.join_eo(0 * fe, fo, L, T), L, T, theta), L, T)[0]
+    ed = torch.from_numpy(np.ascontiguousarray(fe)).cuda()
+    od = torch.from_numpy(np.ascontiguousarray(fo)).cuda()
+    o2 = torch.empty_like(ed)
+    sf.wilson_apply_block(lat, "hop_oe", "fp64", ed, o2)
+    assert relerr(o2.cpu().numpy(), Hx_oe) <= 1e-12
+    sf.wilson_apply_block(lat, "hop_eo", "fp64", od, o2)
+    assert relerr(o2.cpu().numpy(), Hx_eo) <= 1e-12
+    fin = torch.from_numpy(np.ascontiguousarray(np.stack([fe, fo], axis=0))).cuda()
+    fout = torch.empty_like(fin)
+    sf.wilson_apply_block(lat, "d_full", "fp64", fin, fout)
+    Dref = oracle.apply_D(U, full, L, T, theta, kappa)
+    De, Do = oracle.split_eo(Dref, L, T)
+    assert relerr(fout.cpu().numpy(), np.stack([De, Do], axis=0)) <= 1e-12
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 4e-3)])
+def test_apply_low_precision_within_storage_precision(sf, prec, tol):
+    L, T, eps, kappa, theta = 6, 7, 0.3, 0.13, 0.5
+    U, lat = _lattice(sf, L, T, eps, kappa, theta)
+    x = inputs.sources(L, T, 5, 97)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    for op, dag in (("dhat", False), ("dhat_dag", True)):
+        sf.wilson_apply_block(lat, op, prec, xd, out)
+        ref = oracle.apply_dhat(U, x, L, T, theta, kappa, dagger=dag)
+        assert relerr(out.cpu().numpy(), ref) <= tol, (prec, op)
+    lat.close()
+
+
+def test_tilings_agree(sf):
+    """Every (TS, NR) tiling computes the same sites: bitwise equal across
+    tile sizes for one RHS-block width (same kernel), and equal to rounding
+    across widths (separate instantiations may contract into FMAs differently)."""
+    L, T, eps, kappa, theta = 6, 6, 0.3, 0.13, 0.5
+    U = inputs.links(L, T, eps, 55)
+    x = torch.from_numpy(inputs.sources(L, T, 5, 56)).cuda()
+    outs = {}
+    for prec, nrs in (("fp64", (1, 2)), ("fp32", (1, 2, 3, 5)), ("fp16", (1, 2, 3, 5))):
+        for TS in (32, 64, 128):
+            for NR in nrs:
+                RG = -(-5 // NR)
+                lim = {"fp64": 256 if NR == 1 else 128}.get(prec, 512 if NR == 1 else 384 if NR == 2 else 256)
+                if TS * RG > lim:
+                    continue
+                lat = sf.Lattice(L, T, theta, kappa, 4.52, torch.from_numpy(U).cuda())
+                lat.set_tuning(prec, TS, NR)
+                o = torch.empty_like(x)
+                sf.wilson_apply_block(lat, "dhat", prec, x, o)
+                outs.setdefault(prec, []).append(((TS, NR), o.cpu().numpy()))
+                lat.close()
+    for prec, lst in outs.items():
+        by_nr = {}
+        for (TS, NR), o in lst:
+            by_nr.setdefault(NR, []).append(o)
+        for NR, os_ in by_nr.items():
+            for o in os_[1:]:
+                assert np.array_equal(o, os_[0]), (prec, NR)
+        tol = {"fp64": 1e-15, "fp32": 1e-6, "fp16": 1e-6}[prec]
+        for (TS, NR), o in lst[1:]:
+            assert relerr(o, lst[0][1]) <= tol, (prec, TS, NR)
+
+
+def test_host_and_device_pointers_agree(sf):
+    L, T, eps, kappa, theta = 4, 6, 0.3, 0.125, 0.5
+    U = inputs.links(L, T, eps, 11)
+    x = inputs.sources(L, T, 2, 12)
+    lat_h = sf.Lattice(L, T, theta, kappa, 4.52, U)
+    out_h = np.empty_like(x)
+    sf.wilson_apply_block(lat_h, "dhat", "fp64", x, out_h)
+    xd = torch.from_numpy(x).cuda()
+    out_d = torch.empty_like(xd)
+    sf.wilson_apply_block(lat_h, "dhat", "fp64", xd, out_d)
+    assert np.array_equal(out_h, out_d.cpu().numpy())
+    lat_h.close()
+
+
+@pytest.mark.parametrize("algo", ["bicgstab", "mixed_dc", "mixed_dc_half"])
+def test_solve_sf8_plain_config(sf, algo):
+    """8^3x8 SF, eps 0.3, kappa 0.125, theta 0.5, 1 RHS, solved to 1e-12."""
+    w = inputs.workload("sf8_plain_1rhs")
+    lt = w.lattices[0]
+    U = lt.make_links()
+    phi = lt.make_sources(1)
+    lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(U).cuda())
+    X = torch.empty_like(torch.from_numpy(phi)).cuda()
+    Y = torch.empty_like(X)
+    info = sf.solve_block(lat, algo, torch.from_numpy(phi).cuda(), X, Y, tol=w.tol, maxiter=5000)
+    Xn, Yn = X.cpu().numpy(), Y.cpu().numpy()
+    rx = oracle.true_residual(U, phi, Xn, lt.L, lt.T, lt.theta, lt.kappa)
+    ry = oracle.true_residual(U, Xn, Yn, lt.L, lt.T, lt.theta, lt.kappa, dagger=True)
+    assert np.all(rx <= w.tol * 1.05), (rx, info)
+    assert np.all(ry <= w.tol * 1.05), (ry, info)
+    # the library's own FP64 recomputation agrees with the oracle's
+    assert np.allclose(info["true_resid"], rx, rtol=1e-3, atol=w.tol * 1e-3)
+    lat.close()
+
+
+def test_solve_five_rhs_and_force_sf12(sf):
+    """12^4 SF, 5 pseudo-fermions, FP32 inner / FP64 outer, 1e-10; force from
+    the GPU's X, Y against the oracle's force from the same X, Y."""
+    w = inputs.workload("sf12_nf10")
+    lt = w.lattices[0]
+    U = lt.make_links()
+    phi = lt.make_sources(w.nrhs)
+    lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(U).cuda())
+    phid = torch.from_numpy(phi).cuda()
+    X = torch.empty_like(phid)
+    Y = torch.empty_like(phid)
+    info = sf.solve_block(lat, "mixed_dc", phid, X, Y, tol=w.tol, maxiter=5000)
+    Xn, Yn = X.cpu().numpy(), Y.cpu().numpy()
+    rx = oracle.true_residual(U, phi, Xn, lt.L, lt.T, lt.theta, lt.kappa)
+    ry = oracle.true_residual(U, Xn, Yn, lt.L, lt.T, lt.theta, lt.kappa, dagger=True)
+    assert np.all(rx <= w.tol * 1.05), (rx, info)
+    assert np.all(ry <= w.tol * 1.05), (ry, info)
+    F = torch.zeros(((lt.T + 1) * lt.L ** 3, 4, 8), dtype=torch.float64, device="cuda")
+    mom = torch.ones_like(F)
+    sf.fermion_force(lat, X, Y, F, mom, eps=0.1)
+    Fo = oracle.force(U, Xn, Yn, lt.L, lt.T, lt.theta, lt.kappa)
+    assert relerr(F.cpu().numpy(), Fo) <= 1e-12
+    assert relerr(mom.cpu().numpy(), 1.0 - 0.1 * Fo) <= 1e-14
+    lat.close()
+
+
+def test_rhs_independence_bitwise(sf):
+    """The result for pseudo-fermion i does not depend on the other fields
+    (Sec. 2: the phi_i are independent): permuting the block permutes the
+    results bitwise, and zero fields stay zero."""
+    L, T, eps, kappa, theta = 6, 6, 0.3, 0.13, 0.5
+    U = inputs.links(L, T, eps, 21)
+    phi = inputs.sources(L, T, 3, 22)
+    lat = sf.Lattice(L, T, theta, kappa, 4.52, torch.from_numpy(U).cuda())
+    lat.set_tuning("fp32", 64, 1)
+    lat.set_tuning("fp64", 64, 1)
+
+    def run(p):
+        pd = torch.from_numpy(np.ascontiguousarray(p)).cuda()
+        X = torch.empty_like(pd)
+        Y = torch.empty_like(pd)
+        sf.solve_block(lat, "mixed_dc", pd, X, Y, tol=1e-10, maxiter=3000)
+        return X.cpu().numpy(), Y.cpu().numpy()
+
+    X0, Y0 = run(phi)
+    perm = [2, 0, 1]
+    X1, Y1 = run(phi[perm])
+    assert np.array_equal(X1, X0[perm]) and np.array_equal(Y1, Y0[perm])
+    z = phi.copy()
+    z[1] = 0
+    X2, Y2 = run(z)
+    assert np.all(X2[1] == 0) and np.all(Y2[1] == 0)
+    lat.close()
+
+
+def test_plaquette_matches_oracle(sf):
+    for (L, T, eps) in ((4, 4, 0.3), (6, 7, 0.5), (8, 8, 0.2)):
+        U = inputs.links(L, T, eps, 31)
+        # non-trivial boundary links too
+        U[: L ** 3, 1:] = inputs.links(L, 2, 0.7, 32)[: L ** 3, 1:]
+        lat = sf.Lattice(L, T, 0.5, 0.13, 4.52, U)
+        S = sf.plaquette_action(lat)
+        So = oracle.plaquette_action(U, L, T, 4.52)
+        assert abs(S - So) <= 1e-12 * abs(So)
+        lat.close()
+
+
+def test_non_su3_links_are_rejected(sf):
+    L, T = 4, 4
+    U = inputs.links(L, T, 0.3, 41)
+    U[17, 2] *= 1.001
+    with pytest.raises(sf.SFError) as e:
+        sf.Lattice(L, T, 0.5, 0.13, 4.52, U)
+    assert e.value.status == sf.SF_ENOTSU3
+    U2 = inputs.links(L, T, 0.3, 41)
+    U2[5, 0, 0, 0] = np.nan
+    with pytest.raises(sf.SFError):
+        sf.Lattice(L, T, 0.5, 0.13, 4.52, U2)
+
+
+def test_set_links_updates_every_precision(sf):
+    L, T, kappa, theta = 6, 6, 0.13, 0.5
+    U1 = inputs.links(L, T, 0.3, 51)
+    U2 = inputs.links(L, T, 0.3, 52)
+    x = inputs.sources(L, T, 2, 53)
+    lat = sf.Lattice(L, T, theta, kappa, 4.52, U1)
+    lat.set_links(torch.from_numpy(U2).cuda())
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    ref = oracle.apply_dhat(U2, x, L, T, theta, kappa)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-6), ("fp16", 4e-3)):
+        sf.wilson_apply_block(lat, "dhat", prec, xd, out)
+        assert relerr(out.cpu().numpy(), ref) <= tol, prec
+    lat.close()
