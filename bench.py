@@ -257,8 +257,8 @@ def run_ours(args, rank, world, local_rank):
     # ---------------- dslash on a lattice larger than L2 (HBM-bound case)
     hbm = None
     if not args.no_hbm_case and rank == 0:
-        Lh, Th = 32, 24
-        Ub = inputs.links(Lh, Th, 0.2, inputs.SEED_BASE + 32, device=dev)
+        Lh, Th = 24, 24
+        Ub = inputs.links(Lh, Th, 0.2, inputs.SEED_BASE + 32)
         big = sf.Lattice(Lh, Th, 0.5, 0.13, 4.52, torch.from_numpy(Ub).to(dev), device=local_rank)
         del Ub
         res = {}
@@ -273,15 +273,97 @@ def run_ours(args, rank, world, local_rank):
             b.record(stream)
             torch.cuda.synchronize()
             t = a.elapsed_time(b) * 1e-3 / 20
+            cold = []
+            for _ in range(20):
+                flush.zero_()
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                sf.wilson_hop_resident(big, p, nrhs, 1)
+                c1.record(stream)
+                cold.append((c0, c1))
+            torch.cuda.synchronize()
+            tc = statistics.mean(c0.elapsed_time(c1) for c0, c1 in cold) * 1e-3
             Vhb = Lh ** 3 * (Th - 1) // 2
             sb = {"fp32": nrhs * 96 * 2 + 8 * 48, "fp16": nrhs * 52 * 2 + 8 * 24}[p]
             ab = Vhb * sb
-            trb = _ncu_traffic(f"hbm32x24:{p}")
+            trb = _ncu_traffic(f"sf24:{p}")
             res[p] = {"achieved": round(ab / t / 1e9, 1), "frac": round(ab / t / 1e9 / peak, 4),
-                      "launch_us": round(t * 1e6, 2), "algorithmic_bytes_per_launch": ab, "TS": TSb, "NR": NRb,
-                      "traffic": trb["dram_bytes_per_launch"] if trb else None}
+                      "launch_us": round(t * 1e6, 2), "achieved_l2_flushed": round(ab / tc / 1e9, 1),
+                      "launch_us_l2_flushed": round(tc * 1e6, 2), "algorithmic_bytes_per_launch": ab,
+                      "TS": TSb, "NR": NRb, "traffic": trb["dram_bytes_per_launch"] if trb else None}
         big.close()
-        hbm = {"lattice": f"{Lh}^3x{Th} SF, 5 RHS (inputs larger than L2)", "unit": "GB/s", "peak": peak, **res}
+        hbm = {"lattice": f"{Lh}^3x{Th} SF, 5 RHS (working set per launch larger than L2)", "unit": "GB/s",
+               "peak": peak, **res}
+
+    # ---------------- solver comparators on the same workload (X and Y, no force)
+    comparators = None
+    if not args.no_comparators:
+        def time_solve(algo, ph, Xo, Yo, reps=3):
+            sf.solve_block(lat, algo, ph, Xo, Yo, tol=tol, maxiter=args.maxiter)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                inf = sf.solve_block(lat, algo, ph, Xo, Yo, tol=tol, maxiter=args.maxiter)
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) / reps, inf
+        comparators = {}
+        for algo in ("bicgstab", "mixed_dc", "mixed_dc_half"):
+            t, inf = time_solve(algo, phi_d, X_d, Y_d)
+            comparators[f"{algo}_block{nrhs}"] = {
+                "ms": round(t * 1e3, 3), "sweeps": [inf["iters_outer"], inf["iters_outer_y"]],
+                "inner_iters": [inf["iters_inner"], inf["iters_inner_y"]],
+                "max_true_rel_resid": max(max(inf["true_resid"]), max(inf["true_resid_y"]))}
+        # the plain FP64 single-RHS solver run once per field, in sequence
+        one = [phi_d[i:i + 1].contiguous() for i in range(nrhs)]
+        X1, Y1 = torch.empty_like(one[0]), torch.empty_like(one[0])
+        sf.solve_block(lat, "bicgstab", one[0], X1, Y1, tol=tol, maxiter=args.maxiter)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        worst = 0.0
+        for i in range(nrhs):
+            inf = sf.solve_block(lat, "bicgstab", one[i], X1, Y1, tol=tol, maxiter=args.maxiter)
+            worst = max(worst, inf["true_resid"][0], inf["true_resid_y"][0])
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        comparators["bicgstab_fp64_single_rhs_x5"] = {"ms": round(t_seq * 1e3, 3), "max_true_rel_resid": worst}
+        best = min(v["ms"] for k, v in comparators.items() if k.startswith("mixed"))
+        comparators["speedup_best_vs_fp64_single_rhs_x5"] = round(t_seq * 1e3 / best, 2)
+        lat.get_tuning("fp64", nrhs)  # restore the 5-RHS workspace
+
+    # ---------------- batched uneven workload: 24 lattices in one launch per kernel
+    batched = None
+    if not args.no_batched and rank == 0:
+        wb = inputs.workload("batched_uneven")
+        blats = [sf.Lattice(b.L, b.T, b.theta, b.kappa, b.beta, torch.from_numpy(b.make_links()).to(dev),
+                            device=local_rank) for b in wb.lattices]
+        bphi = [torch.from_numpy(b.make_sources(wb.nrhs)).to(dev) for b in wb.lattices]
+        bX = [torch.empty_like(p) for p in bphi]
+        bY = [torch.empty_like(p) for p in bphi]
+        batch = sf.Batch(blats, wb.nrhs)
+        batch.solve("mixed_dc", bphi, bX, bY, tol=wb.tol, maxiter=args.maxiter)
+        torch.cuda.synchronize()
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            binfo = batch.solve("mixed_dc", bphi, bX, bY, tol=wb.tol, maxiter=args.maxiter)
+        torch.cuda.synchronize()
+        tb = (time.perf_counter() - t0) / reps
+        for l, bl in enumerate(blats):
+            sf.solve_block(bl, "mixed_dc", bphi[l], bX[l], bY[l], tol=wb.tol, maxiter=args.maxiter)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for l, bl in enumerate(blats):
+            sf.solve_block(bl, "mixed_dc", bphi[l], bX[l], bY[l], tol=wb.tol, maxiter=args.maxiter)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        batched = {"workload": "24 SF fields: 8 each of 8^4, 12^4, 16^4; eps 0.15/0.25/0.35; kappa 0.13; 5 RHS; "
+                               "X and Y to 1e-10, FP32 inner / FP64 outer",
+                   "batched_solves_per_s": round(len(blats) / tb, 2), "batch_ms": round(tb * 1e3, 2),
+                   "one_lattice_at_a_time_ms": round(ts * 1e3, 2), "speedup": round(ts / tb, 2),
+                   "max_true_rel_resid": max(max(max(i["true_resid"]), max(i["true_resid_y"])) for i in binfo)}
+        batch.close()
+        for bl in blats:
+            bl.close()
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -295,6 +377,7 @@ def run_ours(args, rank, world, local_rank):
         "accuracy": {"max_true_rel_resid": resid, "sweeps_x": last["iters_outer"], "inner_iters_x": last["iters_inner"],
                      "sweeps_y": last["iters_outer_y"], "inner_iters_y": last["iters_inner_y"]},
         "roofline": roofline, "dslash_hbm": hbm, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "comparators": comparators, "batched": batched,
     }
     lat.close()
     if rank == 0 and not args.no_cpu_baseline:
@@ -383,6 +466,41 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_dslash_only(args, local_rank):
+    """Hop kernels alone on an L^3 x T lattice with a fixed tiling (for
+    profiler captures): one launch per precision, then `reps` timed ones."""
+    import torch
+    from paper_1009_5169_gb300 import binding as sf
+    from paper_1009_5169_gb300 import inputs
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    L, T = args.dslash_lattice
+    U = inputs.links(L, T, 0.2, inputs.SEED_BASE + 32)
+    lat = sf.Lattice(L, T, 0.5, 0.13, 4.52, torch.from_numpy(U).to(dev), device=local_rank)
+    del U
+    stream = torch.cuda.current_stream(dev)
+    peak, _ = _peaks()
+    res = {}
+    Vh = L ** 3 * (T - 1) // 2
+    for p in args.dslash_precs.split(","):
+        TS, NR = args.tiling
+        lat.set_tuning(p, TS, NR)
+        sf.wilson_hop_resident(lat, p, 5, 1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.reps):
+            sf.wilson_hop_resident(lat, p, 5, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) * 1e-3 / args.reps
+        sb = {"fp64": 5 * 192 * 2 + 8 * 144, "fp32": 5 * 96 * 2 + 8 * 48, "fp16": 5 * 52 * 2 + 8 * 24}[p]
+        res[p] = {"launch_us": round(t * 1e6, 2), "achieved_GBs": round(Vh * sb / t / 1e9, 1),
+                  "frac": round(Vh * sb / t / 1e9 / peak, 4), "algorithmic_bytes_per_launch": Vh * sb}
+    lat.close()
+    print(json.dumps({"dslash_only": f"{L}^3x{T}", "tiling": args.tiling, "reps": args.reps, **res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,10 +512,20 @@ def main():
     ap.add_argument("--maxiter", type=int, default=5000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hbm-case", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--dslash-only", action="store_true", help="time the hop kernel alone (profiling aid)")
+    ap.add_argument("--dslash-lattice", type=int, nargs=2, default=(32, 24), metavar=("L", "T"))
+    ap.add_argument("--dslash-precs", default="fp32,fp16")
+    ap.add_argument("--tiling", type=int, nargs=2, default=(64, 1), metavar=("TS", "NR"))
+    ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
     rank, world, local_rank = _env_rank()
+    if args.dslash_only:
+        run_dslash_only(args, local_rank)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

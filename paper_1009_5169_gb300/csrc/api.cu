@@ -179,6 +179,8 @@ struct sf_lattice {
         g.L3 = L * L * L;
         g.divLh = make_fastdiv((uint32_t)(L / 2));
         g.divL = make_fastdiv((uint32_t)L);
+        g.L3h = L * L * L / 2;
+        g.divTm1 = make_fastdiv((uint32_t)(T - 1));
         g.kappa = kappa;
         g.ph_re = cos(theta / L);
         g.ph_im = sin(theta / L);
@@ -262,7 +264,10 @@ struct Workspace {
         CK(cudaMemset(ost.p, 0, n * sizeof(OState)));
         // the most blocks any tiling can use: TS = 32
         long long maxblk = 0;
-        for (int l = 0; l < nlat; ++l) maxblk += std::min((ls[l]->Vh + 31) / 32, 8 * sm_count);
+        for (int l = 0; l < nlat; ++l) {
+            const int L3h = ls[l]->L * ls[l]->L * ls[l]->L / 2;
+            maxblk += std::min(((L3h + 31) / 32) * (ls[l]->T - 1), 8 * sm_count);
+        }
         partials.ensure((size_t)3 * nrhs * maxblk * sizeof(double));
         counters.ensure((size_t)nlat * sizeof(unsigned));
         CK(cudaMemset(counters.p, 0, (size_t)nlat * sizeof(unsigned)));
@@ -282,7 +287,7 @@ struct Workspace {
         for (int l = 0; l < nlat; ++l) {
             LatDev g = lats[l]->base_desc();
             g.soff = soff[l];
-            g.ntiles = (g.Vh + TS - 1) / TS;
+            g.ntiles = ((g.L3h + TS - 1) / TS) * (g.T - 1);  // time-slice-fastest tiles
             g.nblk = std::min(g.ntiles, 8 * sm_count);
             g.blk0 = blk;
             blk += g.nblk;
@@ -514,7 +519,7 @@ std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 
 int maxt(int ci, int NR) {
     if (ci == 0) return NR == 1 ? 256 : 128;
-    return NR == 1 ? 512 : NR == 2 ? 384 : 256;
+    return NR == 1 ? 320 : NR == 2 ? 384 : 256;
 }
 
 }  // namespace

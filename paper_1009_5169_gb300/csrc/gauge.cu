@@ -337,7 +337,7 @@ cudaError_t launch_outer_check(int n, OState* ost, const double* rr, const doubl
 }
 
 template <int NR>
-__global__ void __launch_bounds__(KB<P64, NR>::MAXT) k_norm2(const LatDev* __restrict__ lats, int nlat, int nrhs,
+__global__ void __launch_bounds__(KB<P64, NR>::MAXT, KB<P64, NR>::MINB) k_norm2(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                 CField<P64> f, SolverCtx ctx, double* __restrict__ out) {
     __shared__ double sres[MAX_RHS * 3];
     const int l = find_lattice(lats, nlat, blockIdx.x);
@@ -347,9 +347,9 @@ __global__ void __launch_bounds__(KB<P64, NR>::MAXT) k_norm2(const LatDev* __res
     double red[NR][1];
 #pragma unroll
     for (int j = 0; j < NR; ++j) red[j][0] = 0.0;
-    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
-        const int cb = tile * blockDim.x + threadIdx.x;
-        if (cb >= g.Vh) break;
+    for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (j >= nval) continue;

@@ -52,10 +52,14 @@ __device__ __forceinline__ long long sbase(const LatDev& g, int rhs) { return g.
 
 // Threads per block a kernel of a (precision, NR) configuration may be
 // launched with; it sets the register budget 65536 / MAXT per thread.
+// FP32/FP16 with NR = 1 is held to 96 registers (two 320-thread blocks per
+// SM): the hop is latency-bound and gains more from resident warps than from
+// the extra load hoisting a larger budget buys.
 template <typename P, int NR>
 struct KB {
-    static constexpr int MAXT = std::is_same<P, P64>::value ? (NR == 1 ? 256 : 128)
-                                                           : (NR == 1 ? 512 : NR == 2 ? 384 : 256);
+    static constexpr bool F64 = std::is_same<P, P64>::value;
+    static constexpr int MAXT = F64 ? (NR == 1 ? 256 : 128) : (NR == 1 ? 320 : NR == 2 ? 384 : 256);
+    static constexpr int MINB = F64 ? 1 : (NR == 1 ? 2 : 1);
 };
 
 // ------------------------------------------------------------ hop
@@ -220,7 +224,7 @@ __device__ __forceinline__ bool rhs_active(const KState* st, int idx) { return s
 // ------------------------------------------------------------ kernels
 // out(out_par) = coef * H in
 template <typename PI, typename PO, int NR, bool DAG>
-__global__ void __launch_bounds__(KB<PI, NR>::MAXT) k_hop(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
+__global__ void __launch_bounds__(KB<PI, NR>::MAXT, KB<PI, NR>::MINB) k_hop(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
                                               CField<PI> in, Field<PO> out, double coef, int kpow,
                                               const KState* __restrict__ st) {
     using R = typename PI::real;
@@ -234,9 +238,9 @@ __global__ void __launch_bounds__(KB<PI, NR>::MAXT) k_hop(const LatDev* __restri
         if (j < nval && rhs_active(st, l * nrhs + r0 + j)) any = true;
     if (!any) return;
     const R c = (R)(coef * (kpow == 0 ? 1.0 : kpow == 1 ? g.kappa : g.kappa * g.kappa));
-    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
-        const int cb = tile * blockDim.x + threadIdx.x;
-        if (cb >= g.Vh) break;
+    for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
         const SiteX s = decode_site(g, cb, out_par);
         cpx<R> acc[NR][4][3];
         hop_site<PI, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(KB<PI, NR>::MAXT) k_hop(const LatDev* __restri
 
 // out(out_par) = a * xv + coef * H hin (+ zv) with a fused reduction
 template <typename PH, typename PV, int NR, bool DAG, int RED, bool HASZ>
-__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_tail(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_tail(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
                                                CField<PH> hin, CField<PV> xv, CField<PV> zv, Field<PV> out,
                                                CField<PV> ra, double a, double coef, int kpow,
                                                SolverCtx ctx, double* __restrict__ norm_out) {
@@ -282,9 +286,9 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_tail(const LatDev* __restr
     const RV av = (RV)a;
     const RV cv = (RV)(coef * (kpow == 0 ? 1.0 : kpow == 1 ? g.kappa : g.kappa * g.kappa));
     if (any) {
-        for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
-            const int cb = tile * blockDim.x + threadIdx.x;
-            if (cb >= g.Vh) break;
+        for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+            const int cb = tile_cb(g, tile, threadIdx.x);
+            if (cb < 0) continue;
             const SiteX s = decode_site(g, cb, out_par);
             cpx<RH> acc[NR][4][3];
             hop_site<PH, NR, DAG>(g, s, cb, out_par, hin, r0, nval, acc);
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_tail(const LatDev* __restr
 
 // s = r - alpha v (and its hop-precision copy)
 template <typename PV, typename PH, int NR>
-__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_s_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_s_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                    CField<PV> r, CField<PV> v, Field<PV> s, Field<PH> sh,
                                                    const KState* __restrict__ st) {
     using RV = typename PV::real;
@@ -362,9 +366,9 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_s_update(const LatDev* __r
     const int r0 = threadIdx.y * NR;
     const int nval = min(NR, nrhs - r0);
     constexpr bool COPY = !std::is_same<PV, PH>::value;
-    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
-        const int cb = tile * blockDim.x + threadIdx.x;
-        if (cb >= g.Vh) break;
+    for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (j >= nval) continue;
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_s_update(const LatDev* __r
 
 // x += alpha p + omega s ; r = s - omega t ; rho' = <r0, r>, rr = |r|^2
 template <typename PV, int NR>
-__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_xr_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_xr_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                     Field<PV> x, Field<PV> r, CField<PV> p, CField<PV> s,
                                                     CField<PV> t, CField<PV> r0f, SolverCtx ctx) {
     using RV = typename PV::real;
@@ -408,9 +412,9 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_xr_update(const LatDev* __
             om[j] = cpx<RV>{(RV)k.omega.x, (RV)k.omega.y};
         }
     }
-    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
-        const int cb = tile * blockDim.x + threadIdx.x;
-        if (cb >= g.Vh) break;
+    for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (!act[j]) continue;
@@ -458,7 +462,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_xr_update(const LatDev* __
 
 // p = r + beta (p - omega v); the first block also drives the WHILE node
 template <typename PV, typename PH, int NR>
-__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_p_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_p_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                    Field<PV> p, Field<PH> ph, CField<PV> r, CField<PV> v,
                                                    SolverCtx ctx) {
     using RV = typename PV::real;
@@ -467,9 +471,9 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_p_update(const LatDev* __r
     const LatDev g = lats[l];
     const int r0 = threadIdx.y * NR;
     const int nval = min(NR, nrhs - r0);
-    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
-        const int cb = tile * blockDim.x + threadIdx.x;
-        if (cb >= g.Vh) break;
+    for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (j >= nval) continue;
@@ -502,7 +506,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_p_update(const LatDev* __r
 
 // inner start: b = r64 / |r64|; x = 0, r = r0 = p = b
 template <typename PV, typename PH, int NR>
-__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_inner_init(const LatDev* __restrict__ lats, int nlat, int nrhs,
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_inner_init(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                      CField<P64> r64, Field<PV> x, Field<PV> r, Field<PV> r0f,
                                                      Field<PV> p, Field<PH> ph, SolverCtx ctx, int maxiter) {
     using RV = typename PV::real;
@@ -521,9 +525,9 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_inner_init(const LatDev* _
         act[j] = (j < nval) && ctx.ost[l * nrhs + r0 + j].active;
         inv[j] = act[j] ? ctx.ost[l * nrhs + r0 + j].inv_norm : 0.0;
     }
-    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
-        const int cb = tile * blockDim.x + threadIdx.x;
-        if (cb >= g.Vh) break;
+    for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (!act[j]) continue;
@@ -569,16 +573,16 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_inner_init(const LatDev* _
 
 // x64 += x / inv_norm for the rhs that iterated in this sweep
 template <typename PV, int NR>
-__global__ void __launch_bounds__(KB<PV, NR>::MAXT) k_dc_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_dc_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                     Field<P64> x64, CField<PV> x, SolverCtx ctx) {
     using RV = typename PV::real;
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y * NR;
     const int nval = min(NR, nrhs - r0);
-    for (int tile = blockIdx.x - g.blk0; tile < g.ntiles; tile += g.nblk) {
-        const int cb = tile * blockDim.x + threadIdx.x;
-        if (cb >= g.Vh) break;
+    for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (j >= nval) continue;

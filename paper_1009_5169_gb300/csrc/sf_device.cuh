@@ -94,8 +94,9 @@ struct LatDev {
     const uint2* u16;             // [4][2][3][Vpad]
     long long soff;               // batched-vector offset, in (site, rhs) units
     int blk0, nblk;               // blocks of this lattice in a launch
-    int ntiles;                   // tiles of TS sites
-    int pad_;
+    int ntiles;                   // (T-1) x ceil(L3h / TS) tiles
+    int L3h;                      // sites of one parity in a time slice, L^3 / 2
+    FastDiv divTm1;               // division by T - 1
 };
 
 struct SiteX {
@@ -382,6 +383,27 @@ __device__ __forceinline__ int find_lattice(const LatDev* __restrict__ lats, int
     int l = 0;
     while (l + 1 < nlat && blk >= lats[l + 1].blk0) ++l;
     return l;
+}
+
+// Tiles are ordered time-slice fastest: tile t covers TS consecutive sites
+// of one parity inside the time slice x0 = 1 + t % (T-1), spatial stretch
+// t / (T-1).  A block owns a contiguous range of tiles, so it walks x0 over
+// the same spatial stretch (the x0 +- 1 neighbour slices are reused from one
+// step to the next) and all resident blocks sweep the same few time slices
+// at once (the x1, x2, x3 neighbours are read by blocks running alongside).
+__device__ __forceinline__ int tile_begin(const LatDev& g) {
+    return (int)((long long)(blockIdx.x - g.blk0) * g.ntiles / g.nblk);
+}
+__device__ __forceinline__ int tile_end(const LatDev& g) {
+    return (int)((long long)(blockIdx.x - g.blk0 + 1) * g.ntiles / g.nblk);
+}
+// checkerboard index of lane tx of tile t, or -1 past the end of its slice
+__device__ __forceinline__ int tile_cb(const LatDev& g, int t, int tx) {
+    const uint32_t sp = fdiv((uint32_t)t, g.divTm1);
+    const int x0i = t - (int)sp * (g.T - 1);
+    const int off = (int)sp * (int)blockDim.x + tx;
+    if (off >= g.L3h) return -1;
+    return x0i * g.L3h + off;
 }
 
 }  // namespace sf

@@ -63,26 +63,16 @@ def half_volume(L: int, T: int) -> int:
     return V // 2
 
 
-def _expi_hermitian(H: np.ndarray, eps: float, device=None) -> np.ndarray:
-    """exp(i eps H) for a batch of Hermitian matrices via eigendecomposition.
-
-    With ``device`` (a torch CUDA device) the eigendecomposition runs there,
-    which is much faster for large gauge fields; the Gaussian draws are the
-    same, the result differs only by rounding."""
-    if device is not None:
-        import torch
-        flat = H.reshape(-1, 3, 3)
-        out = np.empty_like(flat)
-        chunk = 1 << 16   # the batched solver's workspace grows with the batch
-        for a in range(0, flat.shape[0], chunk):
-            Ht = torch.from_numpy(flat[a:a + chunk]).to(device)
-            w, V = torch.linalg.eigh(Ht)
-            ph = torch.exp(1j * eps * w.to(torch.complex128))
-            out[a:a + chunk] = ((V * ph[..., None, :]) @ V.conj().transpose(-1, -2)).cpu().numpy()
-        return out.reshape(H.shape)
+def _expi_chunk(H: np.ndarray, eps: float) -> np.ndarray:
     w, V = np.linalg.eigh(H)
     ph = np.exp(1j * eps * w)
     return (V * ph[..., None, :]) @ np.swapaxes(V.conj(), -1, -2)
+
+
+def _expi_hermitian(H: np.ndarray, eps: float, device=None) -> np.ndarray:
+    """exp(i eps H) for a batch of Hermitian matrices via eigendecomposition.
+    (``device`` is accepted for API compatibility and ignored.)"""
+    return _expi_chunk(H, eps)
 
 
 def gaussian_traceless_hermitian(g: np.random.Generator, shape) -> np.ndarray:

@@ -104,7 +104,7 @@ def test_tilings_agree(sf):
         for TS in (32, 64, 128):
             for NR in nrs:
                 RG = -(-5 // NR)
-                lim = {"fp64": 256 if NR == 1 else 128}.get(prec, 512 if NR == 1 else 384 if NR == 2 else 256)
+                lim = {"fp64": 256 if NR == 1 else 128}.get(prec, 320 if NR == 1 else 384 if NR == 2 else 256)
                 if TS * RG > lim:
                     continue
                 lat = sf.Lattice(L, T, theta, kappa, 4.52, torch.from_numpy(U).cuda())
