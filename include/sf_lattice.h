@@ -170,6 +170,24 @@ sf_status plaquette_action(sf_lattice* lat, double* S);
  * one dslash kernel with events on that stream. */
 sf_status wilson_hop_resident(sf_lattice* lat, sf_prec prec, int nrhs, int out_parity);
 
+/* The plaquette action S_g of plaquette_action, for callers that cannot
+ * allocate device memory (a runtime or scheduler that owns the whole device,
+ * or a fixed memory budget handed out by another framework).  The paper has
+ * no counterpart to this call; it exists only for such callers.
+ *   links   device pointer, gauge field in the links layout above;
+ *   S       host or device pointer to one double (device: written on the
+ *           stream, not synchronised; host: the call returns after it);
+ *   device  CUDA device ordinal of links; stream a cudaStream_t or NULL.
+ * Nothing is allocated: the reduction's scratch is a fixed 64.5 KiB array in
+ * the library's device image, held by every GPU that loads the library until
+ * the process exits.  At most 2097152 gauge sites ((T+1) L^3) per call;
+ * larger lattices give SF_EINVAL and no launch.  All calls share the array:
+ * calls whose kernels overlap on the GPU (unordered streams) race and give
+ * wrong results.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture. */
+sf_status plaquette_action_noalloc(int L, int T, double beta, const double* links, double* S, int device,
+                                   void* stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* sf_last_error(void);
 

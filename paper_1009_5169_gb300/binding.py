@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
         L.solve_block.argtypes = [vp, i, i, vp, vp, vp, d, i, ctypes.POINTER(SolveInfo)]
         L.fermion_force.argtypes = [vp, i, vp, vp, vp, vp, d]
         L.plaquette_action.argtypes = [vp, ctypes.POINTER(d)]
+        L.plaquette_action_noalloc.argtypes = [i, i, d, vp, vp, i, vp]
+        L.plaquette_action_noalloc.restype = ctypes.c_int
         L.sf_last_error.restype = ctypes.c_char_p
         L.sf_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), i]
         L.sf_batch_solve.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i,

@@ -661,6 +661,14 @@ extern "C" {
 
 const char* sf_last_error(void) { return g_err.c_str(); }
 
+}  // extern "C"
+
+namespace sf {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace sf
+
+extern "C" {
+
 sf_status sf_lattice_create(sf_lattice** out, int L, int T, double theta, double kappa, double beta,
                             const double* links, int device, void* stream) {
     return guarded([&] {
