@@ -184,6 +184,8 @@ struct sf_lattice {
         g.kappa = kappa;
         g.ph_re = cos(theta / L);
         g.ph_im = sin(theta / L);
+        g.ph3_re = cos(3.0 * theta / L);
+        g.ph3_im = sin(3.0 * theta / L);
         g.u64 = u64.as<double2>();
         g.u32 = u32.as<float4>();
         g.u16 = u16.as<uint2>();
@@ -650,8 +652,7 @@ void upload_links(sf_lattice* lat, const double* links) {
         throw SfError{SF_ENOTSU3, buf};
     }
     const LatDev g = lat->base_desc();
-    CK(launch_link_prep(g, lat->canon.as<double>(), lat->u64.as<double2>(), lat->u32.as<float4>(),
-                        lat->u16.as<uint2>(), lat->stream));
+    CK(launch_link_prep(g, lat->canon.as<double>(), lat->stream));
 }
 
 }  // namespace

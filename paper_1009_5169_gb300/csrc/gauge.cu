@@ -9,7 +9,10 @@ namespace sf {
 
 // ------------------------------------------------------------ link prep
 // canon: [(T+1) L^3][mu][3][3] complex FP64; fermion site (par, cb) has gauge
-// index lex + L^3.  Writes every (mu, parity, cb) of the fermion lattice.
+// index lex + L^3.  Writes every (mu, parity, cb) of the fermion lattice in
+// the three hop layouts (FP64 all 18 reals, FP32 and FP16 rows 0 and 1),
+// spatial links multiplied by the twist phase e^{i theta/L} in FP64 before
+// rounding.
 __global__ void k_link_prep(LatDev g, const double2* __restrict__ canon, double2* __restrict__ u64,
                             float4* __restrict__ u32, uint2* __restrict__ u16) {
     const int par = blockIdx.y;
@@ -21,11 +24,15 @@ __global__ void k_link_prep(LatDev g, const double2* __restrict__ canon, double2
             const double2* src = canon + (gi * 4 + mu) * 9;
             double2 m[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) m[k] = src[k];
-            const long long b9 = ((long long)(mu * 2 + par) * 9) * g.Vpad + cb;
+            for (int k = 0; k < 9; ++k) {
+                const double2 v = src[k];
+                m[k] = (mu == 0) ? v : make_double2(g.ph_re * v.x - g.ph_im * v.y, g.ph_re * v.y + g.ph_im * v.x);
+            }
+            const long long pl = (long long)(mu * 2 + par);
+            const long long b9 = pl * 9 * g.Vpad + cb;
 #pragma unroll
             for (int k = 0; k < 9; ++k) u64[b9 + (long long)k * g.Vpad] = m[k];
-            const long long b3 = ((long long)(mu * 2 + par) * 3) * g.Vpad + cb;
+            const long long b3 = pl * 3 * g.Vpad + cb;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const double2 a = m[2 * k], b = m[2 * k + 1];
@@ -39,11 +46,11 @@ __global__ void k_link_prep(LatDev g, const double2* __restrict__ canon, double2
     }
 }
 
-cudaError_t launch_link_prep(const LatDev& g, const double* canon, double2* u64, float4* u32, uint2* u16,
-                             cudaStream_t st) {
+cudaError_t launch_link_prep(const LatDev& g, const double* canon, cudaStream_t st) {
     const int blocks = (g.Vh + 255) / 256;
-    k_link_prep<<<dim3(blocks < 1 ? 1 : blocks, 2), 256, 0, st>>>(g, reinterpret_cast<const double2*>(canon), u64,
-                                                                   u32, u16);
+    k_link_prep<<<dim3(blocks < 1 ? 1 : blocks, 2), 256, 0, st>>>(
+        g, reinterpret_cast<const double2*>(canon), const_cast<double2*>(g.u64), const_cast<float4*>(g.u32),
+        const_cast<uint2*>(g.u16));
     return cudaGetLastError();
 }
 
@@ -200,9 +207,10 @@ cudaError_t launch_plaquette(int L, int T, double beta, const double* canon, dou
 
 // ------------------------------------------------------------ force
 // For the link U_mu(x) with both ends on the fermion lattice:
-//   M1 = lambda   sum_i sum_s Xh_i(x+mu)_s [(1-gamma_mu) Yh_i(x)]_s^dag
-//   M2 = lambda^* sum_i sum_s Xh_i(x)_s    [(1+gamma_mu) Yh_i(x+mu)]_s^dag
-//   W  = U M1 - M2 U^dag,   F^a = -2 kappa Im tr[T^a W] = -kappa Im tr[lambda^a W].
+//   M1 = sum_i sum_s Xh_i(x+mu)_s [(1-gamma_mu) Yh_i(x)]_s^dag
+//   M2 = sum_i sum_s Xh_i(x)_s    [(1+gamma_mu) Yh_i(x+mu)]_s^dag
+//   W  = lambda U M1 - lambda^* M2 U^dag,
+//   F^a = -2 kappa Im tr[T^a W] = -kappa Im tr[lambda^a W]  (lambda^a Gell-Mann).
 // Because (1 -+ gamma_mu) = sum_k v_k v_k^dag with the two spin vectors that
 // define the half spinors of the hop, each spin sum is two colour outer
 // products of half spinors: M = sum_k h_k(X) h_k(Y)^dag.
@@ -242,9 +250,10 @@ __device__ __forceinline__ void force_dir(const LatDev& g, const SiteX& s, int c
 #pragma unroll
                 for (int b = 0; b < 3; ++b) M2[a][b] = M2[a][b] + hX[k][a] * conj(hY[k][b]);
     }
-    Link<double> U;
-    load_link(g, g.u64, MU, par, cb, U);
-    cpx<double> lam = (MU == 0) ? cpx<double>{1.0, 0.0} : cpx<double>{g.ph_re, g.ph_im};
+    // the stored link is V = lambda U, so lambda U M1 = V M1 and
+    // lambda^* M2 U^dag = M2 V^dag: W = V M1 - M2 V^dag
+    Link<double> V;
+    LinkLoad<P64>::load<MU>(g, par, cb, V);
     cpx<double> W[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -253,10 +262,10 @@ __device__ __forceinline__ void force_dir(const LatDev& g, const SiteX& s, int c
             cpx<double> t1{0, 0}, t2{0, 0};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                cfma(t1, U.m[a][k], M1[k][b]);
-                t2 = t2 + M2[a][k] * conj(U.m[b][k]);
+                cfma(t1, V.m[a][k], M1[k][b]);
+                t2 = t2 + M2[a][k] * conj(V.m[b][k]);
             }
-            W[a][b] = lam * t1 - conj(lam) * t2;
+            W[a][b] = t1 - t2;
         }
     const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
     double f[8];

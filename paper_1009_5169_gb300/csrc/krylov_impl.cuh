@@ -7,8 +7,8 @@
 // Schroedinger-functional boundaries used by the paper's SF runs, Sec. 4):
 //   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) lambda_mu psi(x+mu)
 //              + (1 + gamma_mu) U_mu(x-mu)^dag lambda_mu^* psi(x-mu),
-//   lambda_0 = 1, lambda_k = e^{i theta/L}; time hops leaving x0 = 1..T-1 are
-//   dropped (Dirichlet).  Even/odd preconditioning (Sec. 3.1):
+//   lambda_0 = 1, lambda_k = e^{i theta/L} (stored inside the spatial links,
+//   V_k = lambda_k U_k); time hops leaving x0 = 1..T-1 are dropped (Dirichlet).  Even/odd preconditioning (Sec. 3.1):
 //   Dhat = 1 - kappa^2 H_eo H_oe,  Dhat^dag = gamma_5 Dhat gamma_5, where
 //   gamma_5 H gamma_5 swaps the projectors (1 -+ gamma_mu).
 // Each block owns a lattice's tiles of TS sites x (nrhs / NR) groups of NR
@@ -22,11 +22,6 @@
 #include "sf_kernels.h"
 
 namespace sf {
-
-template <typename P> struct LinkOf;
-template <> struct LinkOf<P64> { static __device__ __forceinline__ const double2* ptr(const LatDev& g) { return g.u64; } };
-template <> struct LinkOf<P32> { static __device__ __forceinline__ const float4* ptr(const LatDev& g) { return g.u32; } };
-template <> struct LinkOf<P16> { static __device__ __forceinline__ const uint2* ptr(const LatDev& g) { return g.u16; } };
 
 template <typename P> __host__ __device__ __forceinline__ CField<P> cf(FieldPtr f) {
     return CField<P>{reinterpret_cast<const typename P::vec*>(f.v), f.s};
@@ -70,11 +65,10 @@ __device__ __forceinline__ void hop_dir(const LatDev& g, const SiteX& s, int cb,
     using R = typename P::real;
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma_mu
     constexpr int SB = -SF;
-    const cpx<R> ph = cpx<R>{(R)g.ph_re, (R)g.ph_im};
     if (MU != 0 || s.x0 < g.T - 1) {
         const int ncb = neighbour_cb<MU, +1>(g, s);
         Link<R> U;
-        load_link(g, LinkOf<P>::ptr(g), MU, out_par, cb, U);
+        LinkLoad<P>::template load<MU>(g, out_par, cb, U);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (j < nval) {
@@ -82,12 +76,6 @@ __device__ __forceinline__ void hop_dir(const LatDev& g, const SiteX& s, int cb,
                 load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
                 cpx<R> h[2][3], w[2][3];
                 project<MU, SF>(p, h);
-                if (MU != 0) {
-#pragma unroll
-                    for (int k = 0; k < 2; ++k)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) h[k][a] = ph * h[k][a];
-                }
                 mul_link(U, h, w);
                 expand_add<MU, SF>(acc[j], w);
             }
@@ -96,7 +84,7 @@ __device__ __forceinline__ void hop_dir(const LatDev& g, const SiteX& s, int cb,
     if (MU != 0 || s.x0 > 1) {
         const int ncb = neighbour_cb<MU, -1>(g, s);
         Link<R> U;
-        load_link(g, LinkOf<P>::ptr(g), MU, out_par ^ 1, ncb, U);
+        LinkLoad<P>::template load<MU>(g, out_par ^ 1, ncb, U);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (j < nval) {
@@ -104,12 +92,6 @@ __device__ __forceinline__ void hop_dir(const LatDev& g, const SiteX& s, int cb,
                 load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
                 cpx<R> h[2][3], w[2][3];
                 project<MU, SB>(p, h);
-                if (MU != 0) {
-#pragma unroll
-                    for (int k = 0; k < 2; ++k)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) h[k][a] = conj(ph) * h[k][a];
-                }
                 mul_link_dag(U, h, w);
                 expand_add<MU, SB>(acc[j], w);
             }

@@ -7,9 +7,10 @@
 //   FP32 spinor   float4  [rhs][6][Vpad]    float4 k holds components 2k, 2k+1
 //   FP16 spinor   uint4   [rhs][3][Vpad]    8 halves = components 4k..4k+3,
 //                 float   [rhs][Vpad]       times a per-(site, rhs) scale
-//   FP64 links    double2 [mu][parity][9][Vpad]   full 3x3
-//   FP32 links    float4  [mu][parity][3][Vpad]   rows 0,1 (row 2 rebuilt)
-//   FP16 links    uint2   [mu][parity][3][Vpad]   rows 0,1 (row 2 rebuilt)
+//   FP64 links    double2 [mu][parity][9][Vpad]   complex 0..8 of the 3x3
+//   FP32 links    float4  [mu][parity][3][Vpad]   rows 0, 1 (row 2 rebuilt)
+//   FP16 links    uint2   [mu][parity][3][Vpad]   rows 0, 1 (row 2 rebuilt)
+//   spatial links times the twist phase e^{i theta/L} (see LinkLoad)
 // Sites of one parity are numbered in lexicographic order of the fermion
 // lattice x0 = 1..T-1, x1..x3 = 0..L-1 (x3 fastest): cb = lex / 2 for even L.
 // Batched vectors put lattice l's block at element offset soff_l * (planes
@@ -88,10 +89,11 @@ struct LatDev {
     int L2, L3;
     FastDiv divLh, divL;
     double kappa;
-    double ph_re, ph_im;          // e^{i theta / L} on forward spatial hops
-    const double2* u64;           // [4][2][9][Vpad]
-    const float4* u32;            // [4][2][3][Vpad]
-    const uint2* u16;             // [4][2][3][Vpad]
+    double ph_re, ph_im;          // lambda = e^{i theta / L}, folded into the stored spatial links
+    double ph3_re, ph3_im;        // lambda^3 (third-row rebuild of the 12-real links)
+    const double2* u64;           // [4][2][9][Vpad]  complex 0..8
+    const float4* u32;            // [4][2][3][Vpad]  rows 0, 1
+    const uint2* u16;             // [4][2][3][Vpad]  rows 0, 1 (halves)
     long long soff;               // batched-vector offset, in (site, rhs) units
     int blk0, nblk;               // blocks of this lattice in a launch
     int ntiles;                   // (T-1) x ceil(L3h / TS) tiles
@@ -300,54 +302,79 @@ __device__ __forceinline__ void store_spinor<P16, float>(const Field<P16>& f, lo
 
 // ------------------------------------------------------ links
 // Links of a hop: U_mu(x) at the output site (forward) or U_mu(x - mu) at the
-// neighbour (backward), both addressed by (mu, parity, cb).
+// neighbour (backward), both addressed by (mu, parity, cb).  The stored
+// spatial links carry the twist phase: V_k(x) = e^{i theta/L} U_k(x), so the
+// forward hop needs V_k(x) and the backward hop V_k(x-k)^dag with no further
+// phase factor.  V_k is in U(3): FP64 stores all 18 reals, FP32/FP16 two
+// rows and rebuild the third with the phase (rebuild_row2).
 template <typename R>
 struct Link {
     cpx<R> m[3][3];
 };
 
-__device__ __forceinline__ void load_link(const LatDev& g, const double2* __restrict__ u, int mu, int par,
-                                          int cb, Link<double>& U) {
-    const double2* b = u + ((long long)(mu * 2 + par) * 9) * g.Vpad + cb;
+template <typename P> struct LinkLoad;
+
+template <>
+struct LinkLoad<P64> {
+    template <int MU>
+    static __device__ __forceinline__ void load(const LatDev& g, int par, int cb, Link<double>& U) {
+        const double2* b = g.u64 + ((long long)(MU * 2 + par) * 9) * g.Vpad + cb;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        double2 v = __ldg(b + (long long)k * g.Vpad);
-        U.m[k / 3][k % 3] = cpx<double>{v.x, v.y};
+        for (int k = 0; k < 9; ++k) {
+            double2 v = __ldg(b + (long long)k * g.Vpad);
+            U.m[k / 3][k % 3] = cpx<double>{v.x, v.y};
+        }
     }
+};
+
+// FP32 and FP16 keep the first two rows only.  For V = lambda U with U in
+// SU(3) the third row is lambda^3 conj(row0 x row1) (lambda = 1 in time).
+template <int MU, typename R>
+__device__ __forceinline__ void rebuild_row2(const LatDev& g, Link<R>& U) {
+    cpx<R> c0 = conj(U.m[0][1] * U.m[1][2] - U.m[0][2] * U.m[1][1]);
+    cpx<R> c1 = conj(U.m[0][2] * U.m[1][0] - U.m[0][0] * U.m[1][2]);
+    cpx<R> c2 = conj(U.m[0][0] * U.m[1][1] - U.m[0][1] * U.m[1][0]);
+    if (MU != 0) {
+        const cpx<R> l3 = cpx<R>{(R)g.ph3_re, (R)g.ph3_im};
+        c0 = l3 * c0;
+        c1 = l3 * c1;
+        c2 = l3 * c2;
+    }
+    U.m[2][0] = c0;
+    U.m[2][1] = c1;
+    U.m[2][2] = c2;
 }
 
-// third row of an SU(3) matrix from the first two: row2 = conj(row0 x row1)
-template <typename R>
-__device__ __forceinline__ void rebuild_row2(Link<R>& U) {
-    U.m[2][0] = conj(U.m[0][1] * U.m[1][2] - U.m[0][2] * U.m[1][1]);
-    U.m[2][1] = conj(U.m[0][2] * U.m[1][0] - U.m[0][0] * U.m[1][2]);
-    U.m[2][2] = conj(U.m[0][0] * U.m[1][1] - U.m[0][1] * U.m[1][0]);
-}
-
-__device__ __forceinline__ void load_link(const LatDev& g, const float4* __restrict__ u, int mu, int par,
-                                          int cb, Link<float>& U) {
-    const float4* b = u + ((long long)(mu * 2 + par) * 3) * g.Vpad + cb;
+template <>
+struct LinkLoad<P32> {
+    template <int MU>
+    static __device__ __forceinline__ void load(const LatDev& g, int par, int cb, Link<float>& U) {
+        const float4* b = g.u32 + ((long long)(MU * 2 + par) * 3) * g.Vpad + cb;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        float4 v = __ldg(b + (long long)k * g.Vpad);
-        U.m[(2 * k) / 3][(2 * k) % 3] = cpx<float>{v.x, v.y};
-        U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = cpx<float>{v.z, v.w};
+        for (int k = 0; k < 3; ++k) {
+            float4 v = __ldg(b + (long long)k * g.Vpad);
+            U.m[(2 * k) / 3][(2 * k) % 3] = cpx<float>{v.x, v.y};
+            U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = cpx<float>{v.z, v.w};
+        }
+        rebuild_row2<MU>(g, U);
     }
-    rebuild_row2(U);
-}
+};
 
-__device__ __forceinline__ void load_link(const LatDev& g, const uint2* __restrict__ u, int mu, int par,
-                                          int cb, Link<float>& U) {
-    const uint2* b = u + ((long long)(mu * 2 + par) * 3) * g.Vpad + cb;
+template <>
+struct LinkLoad<P16> {
+    template <int MU>
+    static __device__ __forceinline__ void load(const LatDev& g, int par, int cb, Link<float>& U) {
+        const uint2* b = g.u16 + ((long long)(MU * 2 + par) * 3) * g.Vpad + cb;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        uint2 v = __ldg(b + (long long)k * g.Vpad);
-        float2 a = h2f(v.x), c = h2f(v.y);
-        U.m[(2 * k) / 3][(2 * k) % 3] = cpx<float>{a.x, a.y};
-        U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = cpx<float>{c.x, c.y};
+        for (int k = 0; k < 3; ++k) {
+            uint2 v = __ldg(b + (long long)k * g.Vpad);
+            const float2 a = h2f(v.x), c = h2f(v.y);
+            U.m[(2 * k) / 3][(2 * k) % 3] = cpx<float>{a.x, a.y};
+            U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = cpx<float>{c.x, c.y};
+        }
+        rebuild_row2<MU>(g, U);
     }
-    rebuild_row2(U);
-}
+};
 
 // u = U h (two colour vectors)
 template <typename R>

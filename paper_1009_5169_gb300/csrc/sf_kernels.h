@@ -106,8 +106,8 @@ cudaError_t launch_outer_check(int n, OState* ost, const double* rr, const doubl
 cudaError_t launch_norm2(const LaunchCfg&, FieldPtr f64, const SolverCtx*, double* out, cudaStream_t);
 
 // link preparation: canonical AoS FP64 gauge field -> kernel layouts
-cudaError_t launch_link_prep(const LatDev& g, const double* canon, double2* u64, float4* u32, uint2* u16,
-                             cudaStream_t);
+// (writes the link arrays g points at)
+cudaError_t launch_link_prep(const LatDev& g, const double* canon, cudaStream_t);
 // max |U^dag U - 1| and max |det U - 1| over the gauge field's links
 cudaError_t launch_su3_check(int L, int T, const double* canon, unsigned long long* out2, cudaStream_t);
 cudaError_t launch_plaquette(int L, int T, double beta, const double* canon, double* partials,
