@@ -96,7 +96,16 @@ typedef enum {
     /* FP64 defect correction around an FP32 BiCGStab (Sec. 3.2) */
     SF_SOLVE_MIXED_DC = 1,
     /* FP64 defect correction around BiCGStab with FP16 hop operands */
-    SF_SOLVE_MIXED_DC_HALF = 2
+    SF_SOLVE_MIXED_DC_HALF = 2,
+    /* FP64 flexible GCR (restarted, 8 directions) preconditioned by the
+       learned network attached with sf_lattice_set_preconditioner; the FP64
+       true residual judges it, and FP32-inner BiCGStab under FP64 defect
+       correction continues from its iterate if it stops above tol.  One
+       lattice only (not batches). */
+    SF_SOLVE_FGCR_CNN = 3,
+    /* the same FGCR with the identity as preconditioner (the comparison
+       without the network) */
+    SF_SOLVE_FGCR = 4
 } sf_algo;
 
 typedef struct {
@@ -169,6 +178,51 @@ sf_status plaquette_action(sf_lattice* lat, double* S);
  * on the lattice's stream and not synchronised, so a caller can time exactly
  * one dslash kernel with events on that stream. */
 sf_status wilson_hop_resident(sf_lattice* lat, sf_prec prec, int nrhs, int out_parity);
+
+/* ---- learned preconditioner: a 4-layer 3^4-stencil convolutional network
+ * on the full fermion lattice (widths 32 -> H -> H -> H -> 24, ReLU between
+ * layers, H = 16 or 32), BF16 tensor-core kernels with FP32 accumulation.
+ * Input channels: the even-site residual r / s, s = |r| / sqrt(24 V/2) (24
+ * reals per site, zero on odd sites) and Re, Im of tr U_mu(x) / 3 for
+ * mu = 0..3; output: 24 reals per even site; the preconditioner is
+ * M(r) = r + s (out(r/s) - out(-r/s)) / 2 (the network learns the correction
+ * to the identity; M is odd and positively homogeneous).  Parameters
+ * are a flat FP32 array, per layer W[81][c_in][c_out] (offset d in
+ * {-1,0,1}^4, d0 slowest) then the bias [c_out].  The network is an addition
+ * to the paper's method (whose preconditioner is the single-precision solve
+ * of Sec. 3.2); it never decides the answer, the FP64 residual does. */
+typedef struct sf_cnn sf_cnn;
+
+/* Number of parameters for hidden width H (16 or 32); -1 otherwise. */
+long long sf_cnn_num_params(int hidden);
+
+/* Create a network on a device from initial parameters (host or device). */
+sf_status sf_cnn_create(sf_cnn** out, int hidden, const float* params, int device, void* stream);
+
+/* Copy the FP32 master parameters out (host or device). */
+sf_status sf_cnn_get_params(sf_cnn* cnn, float* params);
+
+void sf_cnn_destroy(sf_cnn* cnn);
+
+/* out = M(r) for nrhs even-site fields of the lattice (layout `even`). */
+sf_status sf_cnn_forward(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double* r, double* out);
+
+/* One Adam step (beta 0.9, 0.999) with learning rate lr.  With targets e
+ * (e_i = Dhat^-1 r_i) the loss is the error norm mean_i |M(r_i) - e_i|^2 /
+ * |e_i|^2; with e == NULL it is the residual norm mean_i |r_i - Dhat M(r_i)|^2
+ * / |r_i|^2, differentiated through the FP64 Dhat and Dhat^dag kernels.
+ * *loss receives the loss before the step. */
+sf_status sf_cnn_train_step(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double* r, const double* e, float lr,
+                            double* loss);
+
+/* The gradient of that loss (either mode) with respect to the parameters
+ * (flat layout as the parameters), without updating them. */
+sf_status sf_cnn_gradients(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double* r, const double* e, float* grad,
+                           double* loss);
+
+/* Attach a network as the preconditioner of SF_SOLVE_FGCR_CNN on this
+ * lattice (NULL detaches; the lattice does not own it). */
+sf_status sf_lattice_set_preconditioner(sf_lattice* lat, sf_cnn* cnn);
 
 /* The plaquette action S_g of plaquette_action, for callers that cannot
  * allocate device memory (a runtime or scheduler that owns the whole device,

@@ -17,8 +17,10 @@ this learned one is an addition).  Plain definitions:
 * the network: h0 = X, h_{l+1} = relu(conv_l(h_l)) for l < 3, out = conv_3(h_3);
 * input channels: 24 residual components (spin, colour, re/im) on the even
   sites (zero on odd sites) then 8 link features (Re, Im of tr U_mu(x) / 3 for
-  mu = 0..3), each residual normalised to unit norm; the preconditioner
-  returns |r| out(r / |r|) restricted to the even sites.
+  mu = 0..3), the residual divided by its RMS scale s = |r| / sqrt(24 V/2);
+  the preconditioner returns r + s (out(r/s) - out(-r/s)) / 2 on the even
+  sites (the network learns the correction to the identity; the
+  symmetrisation makes M odd and positively homogeneous).
 
 The GPU stores activations and weights in bfloat16 and accumulates in FP32;
 ``forward(..., bf16=True)`` rounds the same tensors to bfloat16 (round to
@@ -157,10 +159,19 @@ def output_to_even(out, L, T):
     return (o[:, 0:24:2] + 1j * o[:, 1:24:2]).reshape(-1, 4, 3)
 
 
+def rms_scale(r_even) -> float:
+    """s = |r| / sqrt(number of real components): r / s has unit RMS."""
+    r = np.asarray(r_even)
+    return float(np.linalg.norm(r) / np.sqrt(2 * r.size))
+
+
 def precondition(params, U, r_even, L, T, bf16_acts: bool = True):
-    """M(r) = |r| out(r / |r|) on the even sites."""
-    nr = np.linalg.norm(r_even)
-    if nr == 0:
+    """M(r) = r + s (out(r/s) - out(-r/s)) / 2 on the even sites, s the RMS
+    scale of r: the network learns the correction to the identity, and the
+    symmetrisation makes M odd and positively homogeneous, M(a r) = a M(r)."""
+    s = rms_scale(r_even)
+    if s == 0:
         return np.zeros_like(r_even)
-    X = features(U, r_even / nr, L, T)
-    return nr * output_to_even(forward(params, X, L, T, bf16_acts), L, T)
+    op = output_to_even(forward(params, features(U, r_even / s, L, T), L, T, bf16_acts), L, T)
+    om = output_to_even(forward(params, features(U, -r_even / s, L, T), L, T, bf16_acts), L, T)
+    return r_even + s * 0.5 * (op - om)

@@ -26,7 +26,7 @@ STATUS = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOMEM", 3: "SF_ECUDA", 4: "SF_ENOC
           6: "SF_ENOTSU3"}
 OPS = {"dhat": 0, "dhat_dag": 1, "dhatdag_dhat": 2, "d_full": 3, "hop_eo": 4, "hop_oe": 5}
 PRECS = {"fp64": 0, "fp32": 1, "fp16": 2}
-ALGOS = {"bicgstab": 0, "mixed_dc": 1, "mixed_dc_half": 2}
+ALGOS = {"bicgstab": 0, "mixed_dc": 1, "mixed_dc_half": 2, "fgcr_cnn": 3, "fgcr": 4}
 
 
 class SFError(RuntimeError):
@@ -78,6 +78,19 @@ def lib() -> ctypes.CDLL:
         L.plaquette_action.argtypes = [vp, ctypes.POINTER(d)]
         L.plaquette_action_noalloc.argtypes = [i, i, d, vp, vp, i, vp]
         L.plaquette_action_noalloc.restype = ctypes.c_int
+        L.sf_cnn_num_params.argtypes = [i]
+        L.sf_cnn_num_params.restype = ctypes.c_longlong
+        L.sf_cnn_create.argtypes = [ctypes.POINTER(vp), i, vp, i, vp]
+        L.sf_cnn_get_params.argtypes = [vp, vp]
+        L.sf_cnn_destroy.argtypes = [vp]
+        L.sf_cnn_destroy.restype = None
+        L.sf_cnn_forward.argtypes = [vp, vp, i, vp, vp]
+        L.sf_cnn_train_step.argtypes = [vp, vp, i, vp, vp, ctypes.c_float, ctypes.POINTER(d)]
+        L.sf_cnn_gradients.argtypes = [vp, vp, i, vp, vp, vp, ctypes.POINTER(d)]
+        L.sf_lattice_set_preconditioner.argtypes = [vp, vp]
+        for fn in ("sf_cnn_create", "sf_cnn_get_params", "sf_cnn_forward", "sf_cnn_train_step", "sf_cnn_gradients",
+                   "sf_lattice_set_preconditioner"):
+            getattr(L, fn).restype = ctypes.c_int
         L.sf_last_error.restype = ctypes.c_char_p
         L.sf_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), i]
         L.sf_batch_solve.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i,
@@ -275,3 +288,62 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Cnn:
+    """The learned preconditioner's network (see sf_cnn_* in the header)."""
+
+    def __init__(self, hidden: int, params: np.ndarray, device: int = 0, stream: Optional[int] = None):
+        self.hidden = hidden
+        self.nparams = int(lib().sf_cnn_num_params(hidden))
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters, got {p.size}")
+        self._h = ctypes.c_void_p()
+        s = _current_stream(device) if stream is None else stream
+        _check(lib().sf_cnn_create(ctypes.byref(self._h), hidden, _ptr(p), device, s))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparams, np.float32)
+        _check(lib().sf_cnn_get_params(self._h, _ptr(out)))
+        return out
+
+    def forward(self, lat: Lattice, r, out) -> None:
+        nrhs = _nrhs_of(r, lat.Vh * 24 * 8)
+        _check_size(out, nrhs * lat.Vh * 24 * 8, "out")
+        _check(lib().sf_cnn_forward(self._h, lat.handle, nrhs, _ptr(r), _ptr(out)))
+
+    def train_step(self, lat: Lattice, r, e, lr: float) -> float:
+        """e = None trains on the residual norm |r - Dhat M(r)|^2 / |r|^2."""
+        nrhs = _nrhs_of(r, lat.Vh * 24 * 8)
+        if e is not None:
+            _check_size(e, nrhs * lat.Vh * 24 * 8, "e")
+        loss = ctypes.c_double()
+        _check(lib().sf_cnn_train_step(self._h, lat.handle, nrhs, _ptr(r), _ptr(e), lr, ctypes.byref(loss)))
+        return loss.value
+
+    def gradients(self, lat: Lattice, r, e):
+        nrhs = _nrhs_of(r, lat.Vh * 24 * 8)
+        g = np.empty(self.nparams, np.float32)
+        loss = ctypes.c_double()
+        _check(lib().sf_cnn_gradients(self._h, lat.handle, nrhs, _ptr(r), _ptr(e), _ptr(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def close(self) -> None:
+        if self._h:
+            lib().sf_cnn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_preconditioner(lat: Lattice, cnn: Optional[Cnn]) -> None:
+    _check(lib().sf_lattice_set_preconditioner(lat.handle, cnn.handle if cnn is not None else None))

@@ -166,6 +166,7 @@ struct sf_lattice {
     DevMem stage_in, stage_out;  // device staging for host arrays
     int tune_TS[3] = {0, 0, 0}, tune_NR[3] = {0, 0, 0};
     struct Workspace* ws = nullptr;  // own solver workspace (created on first use)
+    sf_cnn* cnn = nullptr;           // learned preconditioner for SF_SOLVE_FGCR_CNN (not owned)
 
     LatDev base_desc() const {
         LatDev g;
@@ -220,7 +221,7 @@ struct Workspace {
         std::vector<LatDev> host;
         LaunchCfg lc{};
         std::vector<LaunchCfg> per_lat;  // pack / unpack / force on lattice l
-    } cfg[3];
+    } cfg[4];  // FP64, FP32, FP16 hop configurations; [3] FP64 BLAS (TS = 32, NR = 1)
 
     FieldBuf phi64, x64, y64, r64, t64o, xo64, yo64;
     struct Inner {
@@ -229,7 +230,8 @@ struct Workspace {
     } inner[3];
 
     DevMem st, ost, partials, counters, loop_count, nrm_bb, nrm_rr, n_active;
-    DevMem io;  // canonical AoS staging for batched pack/unpack
+    DevMem io;   // canonical AoS staging for batched pack/unpack
+    DevMem aux;  // per-rhs scalars of the learned preconditioner's training
     int* pin = nullptr;  // pinned: [0] n_active, [1] loop_count
     std::map<int, std::unique_ptr<GraphEntry>> graphs;
     long long launches = 0;
@@ -402,6 +404,10 @@ struct Workspace {
 
     void ensure_cfg(int ci) {
         if (cfg[ci].ready) return;
+        if (ci == 3) {
+            set_tiling(3, 32, 1);
+            return;
+        }
         // explicit tiling of the (single) lattice wins
         if (nlat == 1 && lats[0]->tune_TS[ci] > 0) {
             set_tiling(ci, lats[0]->tune_TS[ci], lats[0]->tune_NR[ci]);
@@ -430,7 +436,35 @@ struct Workspace {
         bool converged = true;
     };
 
-    Result solve(int ci, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
+    // ---- flexible GCR (FP64) with the learned preconditioner
+    struct Fgcr {
+        static constexpr int M = 8;
+        int m = 0;
+        FieldBuf z[M], w[M];
+        FieldBuf r, g5a, g5b;
+        DevMem ptrs, coef, dots, nrm, norms, invn;
+    };
+    std::unique_ptr<Fgcr> fg;
+
+    void apply_dhat64(bool dag, const FieldBuf& in, FieldBuf& out, cudaStream_t s) {
+        const KrylovOps& o = ops_f64();
+        const LaunchCfg& lc = cfg[0].lc;
+        CK(o.hop(lc, 1, dag, in.ptr(), t64o.ptr(), 1.0, 0, nullptr, s));
+        CK(o.tail(lc, 0, dag, RED_NONE, t64o.ptr(), in.ptr(), FieldPtr{nullptr, nullptr}, out.ptr(),
+                  FieldPtr{nullptr, nullptr}, 1.0, -1.0, 2, nullptr, nullptr, s));
+        launches += 2;
+    }
+
+    // per-rhs complex <a, b> -> host
+    void dots64(const FieldBuf& a, const FieldBuf& b, double2* dev_out, cudaStream_t s) {
+        SolverCtx k = ctx(false);
+        CK(launch_dot64(cfg[3].lc, a.ptr(), b.ptr(), &k, dev_out, s));
+        launches += 1;
+    }
+
+    Result fgcr(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
+
+    Result solve(int ci, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter, bool from_x = false) {
         ensure_cfg(0);
         ensure_cfg(ci);
         ensure_inner(ci);
@@ -446,7 +480,7 @@ struct Workspace {
             e.delta2_floor = floor_delta * floor_delta;
         }
         CK(cudaMemcpyAsync(ost.p, oh.data(), n * sizeof(OState), cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(x.v.p, 0, field_bytes(Prec::F64, S), s));
+        if (!from_x) CK(cudaMemsetAsync(x.v.p, 0, field_bytes(Prec::F64, S), s));
         SolverCtx k0 = ctx(false);
         CK(launch_norm2(cfg[0].lc, phi.ptr(), &k0, nrm_bb.as<double>(), s));
         launches += 1;
@@ -456,7 +490,7 @@ struct Workspace {
         SolverCtx k = ctx(true);
         Result res;
         for (int sweep = 0;; ++sweep) {
-            if (sweep == 0) {
+            if (sweep == 0 && !from_x) {
                 // x = 0: r = phi
                 CK(cudaMemcpyAsync(r64.v.p, phi.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, s));
                 CK(cudaMemcpyAsync(nrm_rr.p, nrm_bb.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -585,6 +619,170 @@ void Workspace::autotune(int ci) {
     set_tiling(ci, bTS, bNR);
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune_cache[key] = {bTS, bNR};
+}
+
+
+// ---------------------------------------------------------------- FGCR
+// Flexible GCR (restarted, m directions) on Dhat x = phi (dag: Dhat^dag) in
+// FP64 with the preconditioner z = M(r): the learned network (with
+// M^dag(r) = gamma_5 M(gamma_5 r) for the adjoint system) or the identity.
+// Directions are orthogonalised in the Dhat-image with two passes of
+// classical Gram-Schmidt.  The answer is judged on a recomputed FP64 residual;
+// if FGCR stops above tolerance, FP32-inner BiCGStab under FP64 defect
+// correction continues from its iterate.
+Workspace::Result Workspace::fgcr(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
+    REQUIRE(nlat == 1, "FGCR runs on a single lattice");
+    ensure_cfg(0);
+    ensure_cfg(3);
+    sf_cnn* cnn = lats[0]->cnn;
+    if (use_cnn) REQUIRE(cnn != nullptr, "no learned preconditioner attached (sf_lattice_set_preconditioner)");
+    cudaStream_t s = stream;
+    const int n = nrhs, m = Fgcr::M;
+    if (!fg) {
+        fg.reset(new Fgcr());
+        fg->m = m;
+        for (int k = 0; k < m; ++k) {
+            fg->z[k].alloc(Prec::F64, S);
+            fg->w[k].alloc(Prec::F64, S);
+        }
+        fg->r.alloc(Prec::F64, S);
+        fg->g5a.alloc(Prec::F64, S);
+        fg->g5b.alloc(Prec::F64, S);
+        std::vector<void*> p(2 * m);
+        for (int k = 0; k < m; ++k) {
+            p[k] = fg->z[k].v.p;
+            p[m + k] = fg->w[k].v.p;
+        }
+        fg->ptrs.ensure(p.size() * sizeof(void*));
+        CK(cudaMemcpy(fg->ptrs.p, p.data(), p.size() * sizeof(void*), cudaMemcpyHostToDevice));
+        fg->coef.ensure((size_t)2 * m * n * sizeof(double2));
+        fg->dots.ensure((size_t)2 * m * n * sizeof(double2));
+        fg->norms.ensure((size_t)n * sizeof(double));
+        fg->invn.ensure((size_t)n * sizeof(double));
+    }
+    const double2* const* zp = fg->ptrs.as<const double2*>();
+    const double2* const* wp = zp + m;
+    const LaunchCfg& bl = cfg[3].lc;
+    const size_t fbytes = field_bytes(Prec::F64, S);
+    std::vector<double2> hd((size_t)2 * m * n), hc((size_t)2 * m * n);
+    auto read_dots = [&](int count) {
+        CK(cudaMemcpyAsync(hd.data(), fg->dots.p, (size_t)count * n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    };
+    auto axpy = [&](const double2* const* xs, int nvec, FieldBuf& y) {
+        CK(cudaMemcpyAsync(fg->coef.p, hc.data(), (size_t)nvec * n * sizeof(double2), cudaMemcpyHostToDevice, s));
+        CK(launch_multi_axpy64(bl, nvec, xs, fg->coef.as<double2>(), y.ptr(), s));
+        launches += 1;
+    };
+    CK(cudaMemsetAsync(x.v.p, 0, fbytes, s));
+    CK(cudaMemcpyAsync(fg->r.v.p, phi.v.p, fbytes, cudaMemcpyDeviceToDevice, s));
+    dots64(phi, phi, fg->dots.as<double2>(), s);
+    read_dots(1);
+    std::vector<double> bb(n), rr(n), nw((size_t)m * n);
+    std::vector<int> iters(n, 0);
+    std::vector<char> done(n);
+    for (int i = 0; i < n; ++i) {
+        bb[i] = hd[i].x;
+        rr[i] = bb[i];
+        done[i] = (bb[i] == 0.0);
+    }
+    auto all_done = [&] {
+        for (char d : done)
+            if (!d) return false;
+        return true;
+    };
+    const CnnLatticeView view{cfg[0].host[0], lats[0]->canon.as<double>(), s, n};
+    std::vector<double> hn(n), hi(n);
+    int total = 0, restarts = 0;
+    while (!all_done() && total < maxiter) {
+        ++restarts;
+        for (int k = 0; k < m && !all_done() && total < maxiter; ++k) {
+            FieldBuf& zk = fg->z[k];
+            FieldBuf& wk = fg->w[k];
+            // z_k = M(r)
+            if (use_cnn) {
+                const double nreal = 24.0 * lats[0]->Vh;
+                for (int i = 0; i < n; ++i) {
+                    hn[i] = sqrt(rr[i] / nreal);  // RMS scale of r
+                    hi[i] = hn[i] > 0 ? 1.0 / hn[i] : 0.0;
+                }
+                CK(cudaMemcpyAsync(fg->norms.p, hn.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+                CK(cudaMemcpyAsync(fg->invn.p, hi.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+                const long long tot = (long long)S * 12;
+                if (dag) {
+                    CK(launch_gamma5_64(tot, lats[0]->Vpad, fg->r.ptr(), fg->g5a.ptr(), s));
+                    CK(cnn_apply_field(cnn, view, fg->g5a.ptr(), fg->norms.as<double>(), fg->invn.as<double>(),
+                                       fg->g5b.ptr()));
+                    CK(launch_gamma5_64(tot, lats[0]->Vpad, fg->g5b.ptr(), zk.ptr(), s));
+                } else {
+                    CK(cnn_apply_field(cnn, view, fg->r.ptr(), fg->norms.as<double>(), fg->invn.as<double>(),
+                                       zk.ptr()));
+                }
+                launches += 8;
+                CK(cudaStreamSynchronize(s));  // the host arrays above are reused next iteration
+            } else {
+                CK(cudaMemcpyAsync(zk.v.p, fg->r.v.p, fbytes, cudaMemcpyDeviceToDevice, s));
+            }
+            // w_k = A z_k, orthogonalised against w_0..w_{k-1} (two passes)
+            apply_dhat64(dag, zk, wk, s);
+            for (int pass = 0; pass < 2 && k > 0; ++pass) {
+                for (int j = 0; j < k; ++j) dots64(fg->w[j], wk, fg->dots.as<double2>() + (size_t)j * n, s);
+                read_dots(k);
+                for (int j = 0; j < k; ++j)
+                    for (int i = 0; i < n; ++i) {
+                        const double d = nw[(size_t)j * n + i];
+                        const double2 v = hd[(size_t)j * n + i];
+                        hc[(size_t)j * n + i] = (d > 0) ? make_double2(-v.x / d, -v.y / d) : make_double2(0, 0);
+                    }
+                axpy(wp, k, wk);
+                axpy(zp, k, zk);
+            }
+            dots64(wk, wk, fg->dots.as<double2>(), s);
+            dots64(wk, fg->r, fg->dots.as<double2>() + n, s);
+            read_dots(2);
+            for (int i = 0; i < n; ++i) {
+                const double d = hd[i].x;
+                nw[(size_t)k * n + i] = d;
+                const double2 v = hd[n + i];
+                hc[i] = (!done[i] && d > 0) ? make_double2(v.x / d, v.y / d) : make_double2(0, 0);
+            }
+            axpy(zp + k, 1, x);
+            for (int i = 0; i < n; ++i) hc[i] = make_double2(-hc[i].x, -hc[i].y);
+            axpy(wp + k, 1, fg->r);
+            dots64(fg->r, fg->r, fg->dots.as<double2>(), s);
+            read_dots(1);
+            for (int i = 0; i < n; ++i) {
+                if (done[i]) continue;
+                rr[i] = hd[i].x;
+                iters[i] += 1;
+                if (!(rr[i] > 0.01 * tol * tol * bb[i])) done[i] = 1;
+            }
+            ++total;
+        }
+    }
+    // judge on the FP64 true residual; continue with BiCGStab where FGCR fell short
+    residual64(dag, phi, x, s);
+    std::vector<double> rt(n);
+    CK(cudaMemcpyAsync(rt.data(), nrm_rr.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    Result res;
+    res.sweeps.assign(n, restarts);
+    res.inner = iters;
+    res.resid.resize(n);
+    bool ok = true;
+    for (int i = 0; i < n; ++i) {
+        res.resid[i] = bb[i] > 0 ? sqrt(rt[i] / bb[i]) : 0.0;
+        if (!(rt[i] <= tol * tol * bb[i])) ok = false;
+    }
+    if (ok) return res;
+    Result fb = solve(1, dag, phi, x, tol, maxiter, /*from_x=*/true);
+    for (int i = 0; i < n; ++i) {
+        res.sweeps[i] += fb.sweeps[i];
+        res.inner[i] += fb.inner[i];
+        res.resid[i] = fb.resid[i];
+    }
+    res.converged = fb.converged;
+    return res;
 }
 
 // ---------------------------------------------------------------- helpers
@@ -878,6 +1076,8 @@ int algo_index(sf_algo a) {
         case SF_SOLVE_BICGSTAB: return 0;
         case SF_SOLVE_MIXED_DC: return 1;
         case SF_SOLVE_MIXED_DC_HALF: return 2;
+        case SF_SOLVE_FGCR_CNN: return 3;
+        case SF_SOLVE_FGCR: return 4;
     }
     throw SfError{SF_EINVAL, "bad algorithm"};
 }
@@ -894,18 +1094,22 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         const int ci = algo_index(algo);
+        const bool fgcr = (ci >= 3);
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.launches = 0;
         w.ensure_cfg(0);
-        w.ensure_cfg(ci);
+        if (!fgcr) w.ensure_cfg(ci);
         cudaStream_t s = lat->stream;
         const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
         const LaunchCfg& pl = w.cfg[0].per_lat[0];
         const double* dphi = to_device(phi, bytes, lat->stage_in, s);
         CK(ops_f64().pack(pl, dphi, w.phi64.ptr(), s));
         w.launches += 1;
-        Workspace::Result rx = w.solve(ci, false, w.phi64, w.x64, tol, maxiter);
+        auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol) {
+            return fgcr ? w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter) : w.solve(ci, dag, rhs, sol, tol, maxiter);
+        };
+        Workspace::Result rx = run(false, w.phi64, w.x64);
         double* dX = out_device(X, bytes, lat->stage_out);
         CK(ops_f64().unpack(pl, w.x64.ptr(), dX, s));
         w.launches += 1;
@@ -913,7 +1117,7 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         Workspace::Result ry;
         bool have_y = false;
         if (Y) {
-            ry = w.solve(ci, true, w.x64, w.y64, tol, maxiter);
+            ry = run(true, w.x64, w.y64);
             have_y = true;
             double* dY = out_device(Y, bytes, lat->stage_out);
             CK(ops_f64().unpack(pl, w.y64.ptr(), dY, s));
@@ -1038,6 +1242,7 @@ sf_status sf_batch_solve(sf_batch* b, sf_algo algo, const double* const* phi, do
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         Workspace& w = b->ws;
         const int ci = algo_index(algo);
+        REQUIRE(ci < 3, "batches run the BiCGStab algorithms");
         CK(cudaSetDevice(w.device));
         w.launches = 0;
         w.ensure_cfg(0);
@@ -1083,6 +1288,148 @@ void sf_batch_destroy(sf_batch* b) {
     cudaSetDevice(b->ws.device);
     if (b->ws.stream) cudaStreamSynchronize(b->ws.stream);
     delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- learned preconditioner
+namespace {
+struct CnnIo {
+    Workspace* w;
+    CnnLatticeView view;
+};
+CnnIo cnn_io(sf_lattice* lat, int nrhs) {
+    Workspace& w = lattice_ws(lat, nrhs);
+    w.ensure_cfg(0);
+    w.ensure_cfg(3);
+    return CnnIo{&w, CnnLatticeView{w.cfg[0].host[0], lat->canon.as<double>(), lat->stream, nrhs}};
+}
+// per-rhs |f|^2 of an FP64 workspace field (host)
+std::vector<double> norms2(Workspace& w, const FieldBuf& f, cudaStream_t s) {
+    w.dots64(f, f, w.ost.as<double2>(), s);  // OState scratch is free outside solves
+    std::vector<double2> h(w.nrhs);
+    CK(cudaMemcpyAsync(h.data(), w.ost.p, w.nrhs * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> out(w.nrhs);
+    for (int i = 0; i < w.nrhs; ++i) out[i] = h[i].x;
+    return out;
+}
+}  // namespace
+
+extern "C" {
+
+sf_status sf_lattice_set_preconditioner(sf_lattice* lat, sf_cnn* cnn) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr, "lattice is NULL");
+        lat->cnn = cnn;
+    });
+}
+
+sf_status sf_cnn_forward(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double* r, double* out) {
+    return guarded([&] {
+        REQUIRE(cnn != nullptr && lat != nullptr && r != nullptr && out != nullptr, "NULL argument");
+        check_nrhs(nrhs);
+        CK(cudaSetDevice(lat->device));
+        CnnIo io = cnn_io(lat, nrhs);
+        Workspace& w = *io.w;
+        cudaStream_t s = lat->stream;
+        const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
+        const LaunchCfg& pl = w.cfg[0].per_lat[0];
+        CK(ops_f64().pack(pl, to_device(r, bytes, lat->stage_in, s), w.phi64.ptr(), s));
+        std::vector<double> n2 = norms2(w, w.phi64, s), nn(nrhs), inv(nrhs);
+        for (int i = 0; i < nrhs; ++i) {
+            nn[i] = sqrt(n2[i] / (24.0 * lat->Vh));  // RMS scale of r
+            inv[i] = nn[i] > 0 ? 1.0 / nn[i] : 0.0;
+        }
+        CK(cudaMemcpyAsync(w.nrm_bb.p, nn.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.nrm_rr.p, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cnn_apply_field(cnn, io.view, w.phi64.ptr(), w.nrm_bb.as<double>(), w.nrm_rr.as<double>(), w.x64.ptr()));
+        double* dout = out_device(out, bytes, lat->stage_out);
+        CK(ops_f64().unpack(pl, w.x64.ptr(), dout, s));
+        finish_out(out, dout, bytes, s);
+        CK(cudaStreamSynchronize(s));
+    });
+}
+
+// one forward + backward on (r, e) pairs: the gradient of the mean relative
+// squared error of the network's correction against e = Dhat^-1 r
+static void cnn_grad_common(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double* r, const double* e, double* loss,
+                            CnnIo& io) {
+    Workspace& w = *io.w;
+    cudaStream_t s = lat->stream;
+    const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
+    const LaunchCfg& pl = w.cfg[0].per_lat[0];
+    CK(ops_f64().pack(pl, to_device(r, bytes, lat->stage_in, s), w.phi64.ptr(), s));
+    std::vector<double> r2 = norms2(w, w.phi64, s), sc(nrhs), inv(nrhs), third(nrhs);
+    for (int i = 0; i < nrhs; ++i) {
+        REQUIRE(r2[i] > 0, "a training residual is zero");
+        sc[i] = sqrt(r2[i] / (24.0 * lat->Vh));  // RMS scale of r
+        inv[i] = 1.0 / sc[i];
+    }
+    w.aux.ensure((size_t)3 * nrhs * sizeof(double));
+    double* d_sc = w.aux.as<double>();
+    double* d_inv = d_sc + nrhs;
+    double* d_3 = d_sc + 2 * nrhs;
+    CK(cudaMemcpyAsync(d_sc, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_inv, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (e) {
+        // error norm: mean_i |M(r_i) - e_i|^2 / |e_i|^2
+        CK(ops_f64().pack(pl, to_device(e, bytes, lat->stage_in, s), w.y64.ptr(), s));
+        std::vector<double> e2 = norms2(w, w.y64, s);
+        for (int i = 0; i < nrhs; ++i) {
+            third[i] = e2[i] * inv[i] * inv[i];
+            REQUIRE(third[i] > 0, "a training target is zero");
+        }
+        CK(cudaMemcpyAsync(d_3, third.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cnn_loss_grad(cnn, io.view, w.phi64.ptr(), w.y64.ptr(), d_inv, d_3, loss));
+        return;
+    }
+    // residual norm: mean_i |r_i - Dhat M(r_i)|^2 / |r_i|^2, whose gradient in
+    // M(r_i) is -2 Dhat^dag (r_i - Dhat M(r_i)) / (n |r_i|^2)
+    CK(cnn_apply_field(cnn, io.view, w.phi64.ptr(), d_sc, d_inv, w.x64.ptr()));
+    w.residual64(false, w.phi64, w.x64, s);
+    w.apply_dhat64(true, w.r64, w.y64, s);
+    std::vector<double> res2(nrhs);
+    CK(cudaMemcpyAsync(res2.data(), w.nrm_rr.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double l = 0.0;
+    for (int i = 0; i < nrhs; ++i) {
+        l += res2[i] / r2[i] / nrhs;
+        third[i] = -sc[i] / (nrhs * r2[i]);
+    }
+    if (loss) *loss = l;
+    CK(cudaMemcpyAsync(d_3, third.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cnn_backward_field(cnn, io.view, w.y64.ptr(), d_3));
+}
+
+sf_status sf_cnn_train_step(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double* r, const double* e, float lr,
+                            double* loss) {
+    return guarded([&] {
+        REQUIRE(cnn != nullptr && lat != nullptr && r != nullptr, "NULL argument");
+        REQUIRE(lr > 0 && lr < 1, "learning rate must be in (0, 1)");
+        check_nrhs(nrhs);
+        CK(cudaSetDevice(lat->device));
+        CnnIo io = cnn_io(lat, nrhs);
+        double l = 0.0;
+        cnn_grad_common(cnn, lat, nrhs, r, e, &l, io);
+        CK(cnn_adam(cnn, lr, lat->stream));
+        CK(cudaStreamSynchronize(lat->stream));
+        if (loss) *loss = l;
+    });
+}
+
+sf_status sf_cnn_gradients(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double* r, const double* e, float* grad,
+                           double* loss) {
+    return guarded([&] {
+        REQUIRE(cnn != nullptr && lat != nullptr && r != nullptr && grad != nullptr, "NULL argument");
+        check_nrhs(nrhs);
+        CK(cudaSetDevice(lat->device));
+        CnnIo io = cnn_io(lat, nrhs);
+        double l = 0.0;
+        cnn_grad_common(cnn, lat, nrhs, r, e, &l, io);
+        CK(cnn_copy_grad(cnn, grad, lat->stream));
+        if (loss) *loss = l;
+    });
 }
 
 }  // extern "C"

@@ -382,4 +382,86 @@ cudaError_t launch_norm2(const LaunchCfg& c, FieldPtr f, const SolverCtx* ctx, d
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ FP64 BLAS for FGCR
+// out[l*nrhs + i] = <a_i, b_i> (complex, sum conj(a) b) for every (lattice, rhs)
+__global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_dot64(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                          CField<P64> a, CField<P64> b, SolverCtx ctx,
+                                                          double2* __restrict__ out) {
+    __shared__ double sres[MAX_RHS * 3];
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y;
+    double red[1][2] = {{0.0, 0.0}};
+    if (r0 < nrhs) {
+        for (int tile = tile_begin(g), te = tile_end(g); tile < te; ++tile) {
+            const int cb = tile_cb(g, tile, threadIdx.x);
+            if (cb < 0) continue;
+            cpx<double> x[4][3], y[4][3];
+            load_spinor<P64, double>(a, vbase<P64>(g, r0), g.Vpad, cb, 0, x);
+            load_spinor<P64, double>(b, vbase<P64>(g, r0), g.Vpad, cb, 0, y);
+            dotc_acc(x, y, red[0][0], red[0][1]);
+        }
+    }
+    if (!reduce_lattice<1, 2>(red, nrhs, l, g, ctx.partials, ctx.counters, sres)) return;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < nrhs) out[l * nrhs + tid] = make_double2(sres[tid * 2], sres[tid * 2 + 1]);
+}
+
+// y_i += sum_j c[j][i] x_j for nvec vectors x_j (coefficients per rhs, device)
+__global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_multi_axpy64(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                                 int nvec, const double2* const* __restrict__ xs,
+                                                                 const double2* __restrict__ c, double2* __restrict__ y) {
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y;
+    if (r0 >= nrhs) return;
+    for (int tile = tile_begin(g), te = tile_end(g); tile < te; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
+        const long long base = vbase<P64>(g, r0) + cb;
+#pragma unroll
+        for (int comp = 0; comp < 12; ++comp) {
+            const long long idx = base + (long long)comp * g.Vpad;
+            double2 acc = y[idx];
+            for (int j = 0; j < nvec; ++j) {
+                const double2 cj = c[j * nlat * nrhs + l * nrhs + r0];
+                const double2 xv = xs[j][idx];
+                acc.x += cj.x * xv.x - cj.y * xv.y;
+                acc.y += cj.x * xv.y + cj.y * xv.x;
+            }
+            y[idx] = acc;
+        }
+    }
+}
+
+// out = gamma_5 in (spin components 2, 3 negated)
+__global__ void k_gamma5_64(long long n_per_rhs_planes, int Vpad, const double2* __restrict__ in, double2* __restrict__ out,
+                            long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int comp = (int)((i / Vpad) % 12);
+        const double2 v = in[i];
+        out[i] = (comp >= 6) ? make_double2(-v.x, -v.y) : v;
+    }
+    (void)n_per_rhs_planes;
+}
+
+cudaError_t launch_dot64(const LaunchCfg& c, FieldPtr a, FieldPtr b, const SolverCtx* ctx, double2* out,
+                         cudaStream_t st) {
+    k_dot64<<<c.nblocks, dim3(c.TS, c.nrhs), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(a), cf<P64>(b), *ctx, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multi_axpy64(const LaunchCfg& c, int nvec, const double2* const* xs, const double2* coef,
+                                FieldPtr y, cudaStream_t st) {
+    k_multi_axpy64<<<c.nblocks, dim3(c.TS, c.nrhs), 0, st>>>(c.lats, c.nlat, c.nrhs, nvec, xs, coef,
+                                                            reinterpret_cast<double2*>(y.v));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gamma5_64(long long total_elems, int Vpad, FieldPtr in, FieldPtr out, cudaStream_t st) {
+    k_gamma5_64<<<4 * 152, 256, 0, st>>>(0, Vpad, reinterpret_cast<const double2*>(in.v),
+                                          reinterpret_cast<double2*>(out.v), total_elems);
+    return cudaGetLastError();
+}
+
 }  // namespace sf

@@ -116,4 +116,33 @@ cudaError_t launch_plaquette(int L, int T, double beta, const double* canon, dou
 cudaError_t launch_force(const LaunchCfg&, FieldPtr xe, FieldPtr xo, FieldPtr ye, FieldPtr yo, double* F,
                          double* mom, double eps, cudaStream_t);
 
+// FGCR building blocks (FP64 fields, one thread per (site, rhs): launch with NR = 1)
+cudaError_t launch_dot64(const LaunchCfg&, FieldPtr a, FieldPtr b, const SolverCtx*, double2* out, cudaStream_t);
+// y += sum_j coef[j][lattice*nrhs + rhs] x_j, xs: device array of nvec field pointers
+cudaError_t launch_multi_axpy64(const LaunchCfg&, int nvec, const double2* const* xs, const double2* coef, FieldPtr y,
+                                cudaStream_t);
+cudaError_t launch_gamma5_64(long long total_elems, int Vpad, FieldPtr in, FieldPtr out, cudaStream_t);
+
+}  // namespace sf
+
+// ---- learned preconditioner (cnn.cu)
+struct sf_cnn;
+namespace sf {
+struct CnnLatticeView {
+    LatDev desc;             // the lattice (batch offset 0)
+    const double* canon;     // device canonical links (features)
+    cudaStream_t stream;
+    int nrhs;
+};
+// z = r + |r| net(r / |r|) on the even sites for FP64 fields r, z of the lattice
+cudaError_t cnn_apply_field(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, const double* norms,
+                            const double* inv_norms, FieldPtr z);
+// forward, loss = mean_b |M(r_b) - e_b|^2 / |e_b|^2, backward into the gradient buffer
+cudaError_t cnn_loss_grad(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, FieldPtr e, const double* inv_norms,
+                          const double* tnorm2, double* loss_host);
+// parameter gradients for d loss / d M(r) = G (FP64 field), coef_b = s_b / 2,
+// after a cnn_apply_field on the same r (its activations are reused)
+cudaError_t cnn_backward_field(sf_cnn* c, const CnnLatticeView& v, FieldPtr G, const double* coef);
+cudaError_t cnn_adam(sf_cnn* c, float lr, cudaStream_t st);
+cudaError_t cnn_copy_grad(sf_cnn* c, float* out, cudaStream_t st);
 }  // namespace sf

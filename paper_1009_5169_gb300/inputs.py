@@ -132,6 +132,37 @@ def su3_directions(shape, seed: int, field_id: int = FIELD_AUX) -> np.ndarray:
     return rng(seed, field_id).standard_normal(tuple(shape) + (8,))
 
 
+def cnn_widths(hidden: int):
+    """Channel widths of the learned preconditioner's four layers."""
+    return [32, hidden, hidden, hidden, 24]
+
+
+def cnn_init_params(hidden: int, seed: int, last_scale: float = 0.05) -> np.ndarray:
+    """Seeded initial parameters (flat FP32: per layer W[81][ci][co], then the
+    bias), Gaussian with variance 2 / (81 ci), zero biases; the last layer is
+    scaled by ``last_scale`` so the preconditioner starts close to the identity."""
+    g = rng(seed, 7)
+    w = cnn_widths(hidden)
+    parts = []
+    for l, (ci, co) in enumerate(zip(w[:-1], w[1:])):
+        sc = np.sqrt(2.0 / (81 * ci)) * (last_scale if l == len(w) - 2 else 1.0)
+        parts.append((g.standard_normal((81, ci, co)) * sc).reshape(-1))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def cnn_unflatten(params: np.ndarray, hidden: int):
+    """[(W [81, ci, co], b [co]), ...] views of a flat parameter array."""
+    w = cnn_widths(hidden)
+    out, off = [], 0
+    for ci, co in zip(w[:-1], w[1:]):
+        n = 81 * ci * co
+        out.append((np.asarray(params[off:off + n], dtype=np.float64).reshape(81, ci, co),
+                    np.asarray(params[off + n:off + n + co], dtype=np.float64)))
+        off += n + co
+    return out
+
+
 # --------------------------------------------------------------------------
 # Workloads: synthetic stand-ins for the paper's 16^4 SF N_f=10 ensemble.
 # --------------------------------------------------------------------------

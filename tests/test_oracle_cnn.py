@@ -132,3 +132,19 @@ def test_features_and_output_roundtrip():
     assert np.array_equal(cnn.output_to_even(out, L, T), r)
     assert np.allclose(X[:, 24], np.real(np.trace(U.reshape(T + 1, L ** 3, 4, 3, 3)[1:T, :, 0], axis1=-2,
                                                    axis2=-1)).reshape(-1) / 3)
+
+
+def test_preconditioner_is_odd_and_homogeneous():
+    """M(-r) = -M(r) and M(a r) = a M(r) exactly (powers of two keep the
+    bfloat16 roundings exact too)."""
+    from paper_1009_5169_gb300 import inputs
+    U = inputs.links(L, T, 0.3, 21)
+    r = inputs.sources(L, T, 1, 22)[0]
+    params = cnn.init_params([32, 8, 8, 8, 24], 23)
+    params = [(W, np.full(W.shape[2], 0.1)) for W, _ in params]   # biases break oddness of the bare net
+    for bf in (False, True):
+        m = cnn.precondition(params, U, r, L, T, bf16_acts=bf)
+        assert np.array_equal(cnn.precondition(params, U, -r, L, T, bf16_acts=bf), -m)
+        assert np.allclose(cnn.precondition(params, U, 4.0 * r, L, T, bf16_acts=bf), 4.0 * m, rtol=0, atol=1e-12)
+    # unit mean square per real component: mean |z|^2 over complex entries is 2
+    assert abs(np.mean(np.abs(r / cnn.rms_scale(r)) ** 2) - 2.0) < 1e-12
