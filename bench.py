@@ -365,6 +365,10 @@ def run_ours(args, rank, world, local_rank):
         for bl in blats:
             bl.close()
 
+    learned = None
+    if not args.no_learned and rank == 0:
+        learned = learned_section(args, dev, local_rank, stream)
+
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
@@ -377,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
         "accuracy": {"max_true_rel_resid": resid, "sweeps_x": last["iters_outer"], "inner_iters_x": last["iters_inner"],
                      "sweeps_y": last["iters_outer_y"], "inner_iters_y": last["iters_inner_y"]},
         "roofline": roofline, "dslash_hbm": hbm, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "comparators": comparators, "batched": batched,
+        "comparators": comparators, "batched": batched, "learned": learned,
     }
     lat.close()
     if rank == 0 and not args.no_cpu_baseline:
@@ -466,6 +470,78 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def learned_section(args, dev, local_rank, stream):
+    """The learned preconditioner on the 24^4 workload (kappa 0.134, eps 0.2,
+    5 RHS, 1e-10): the network is trained on the residual norm with residuals
+    from this library's own solves on seeded 12^4 fields of the same
+    kappa/eps (the network is translation invariant; training on the smaller
+    volume keeps the run short), then FGCR with it is compared on held-out
+    24^4 fields with FGCR without it, plain FP64 BiCGStab and the FP32-inner
+    mixed solve."""
+    import torch
+    from paper_1009_5169_gb300 import binding as sf
+    from paper_1009_5169_gb300 import inputs
+    w = inputs.workload("sf24_cnn")
+    big = w.lattices[0]
+    hidden = 16
+    t0 = time.perf_counter()
+    net = sf.Cnn(hidden, inputs.cnn_init_params(hidden, inputs.SEED_BASE + 40), device=local_rank)
+    train_lats = []
+    samples = []
+    for f in range(args.learned_train_fields):
+        lt = inputs.Lattice(12, 12, big.eps, big.kappa, inputs.SEED_BASE + 4000 + f)
+        lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(lt.make_links()).to(dev),
+                         device=local_rank)
+        phi = torch.from_numpy(inputs.sources(lt.L, lt.T, 5, inputs.SEED_BASE + 4000 + f)).to(dev)
+        X, Y = torch.empty_like(phi), torch.empty_like(phi)
+        sf.solve_block(lat, "mixed_dc", phi, X, Y, tol=1e-8, maxiter=args.maxiter)
+        g5 = torch.tensor([1, 1, -1, -1], dtype=torch.float64, device=dev).view(1, 1, 4, 1)
+        samples.append((lat, phi))
+        samples.append((lat, (X * g5).contiguous()))   # smooth residuals: Dhat (g5 Y) = g5 X
+        train_lats.append(lat)
+    losses = []
+    for epoch in range(args.learned_epochs):
+        for lat, r in samples:
+            losses.append(net.train_step(lat, r, None, 1e-3))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    for lat in train_lats:
+        lat.close()
+    res = {}
+    for h in range(args.learned_heldout):
+        lt = inputs.Lattice(big.L, big.T, big.eps, big.kappa, inputs.SEED_BASE + 1000 + h)
+        lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(lt.make_links()).to(dev),
+                         device=local_rank)
+        sf.set_preconditioner(lat, net)
+        phi = torch.from_numpy(inputs.sources(lt.L, lt.T, w.nrhs, inputs.SEED_BASE + 1000 + h)).to(dev)
+        X, Y = torch.empty_like(phi), torch.empty_like(phi)
+        for algo in ("fgcr_cnn", "fgcr", "bicgstab", "mixed_dc"):
+            if algo == "mixed_dc":   # the others run long enough that one-time set-up is negligible
+                sf.solve_block(lat, algo, phi, X, Y, tol=w.tol, maxiter=args.maxiter)
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            info = sf.solve_block(lat, algo, phi, X, Y, tol=w.tol, maxiter=args.maxiter)
+            torch.cuda.synchronize()
+            e = res.setdefault(algo, {"ms": [], "iters_x": [], "iters_y": [], "max_true_rel_resid": 0.0})
+            e["ms"].append(round((time.perf_counter() - a) * 1e3, 2))
+            e["iters_x"].append(info["iters_inner"])
+            e["iters_y"].append(info["iters_inner_y"])
+            e["max_true_rel_resid"] = max(e["max_true_rel_resid"], max(info["true_resid"]), max(info["true_resid_y"]))
+        sf.set_preconditioner(lat, None)
+        lat.close()
+    net.close()
+    gain_it = statistics.mean(res["fgcr"]["iters_x"]) / max(1e-9, statistics.mean(res["fgcr_cnn"]["iters_x"]))
+    return {"workload": f"{big.L}^3x{big.T} SF, kappa {big.kappa}, eps {big.eps}, {w.nrhs} RHS, tol {w.tol}; "
+                        f"{args.learned_heldout} held-out fields",
+            "network": f"4 x 3^4 conv, widths 32-{hidden}-{hidden}-{hidden}-24, BF16 mma.sync, residual-norm loss",
+            "training": {"fields": f"{args.learned_train_fields} seeded 12^4 fields, residuals phi and g5 X from "
+                                   f"own solves ({len(samples) * 5} residuals)",
+                         "steps": len(losses), "loss_first": round(float(np.mean(losses[:len(samples)])), 4),
+                         "loss_last": round(float(np.mean(losses[-len(samples):])), 4),
+                         "seconds": round(t_train, 1)},
+            "solves": res, "fgcr_iteration_gain_from_network": round(gain_it, 2)}
+
+
 def run_dslash_only(args, local_rank):
     """Hop kernels alone on an L^3 x T lattice with a fixed tiling (for
     profiler captures): one launch per precision, then `reps` timed ones."""
@@ -514,6 +590,10 @@ def main():
     ap.add_argument("--no-hbm-case", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-train-fields", type=int, default=8)
+    ap.add_argument("--learned-epochs", type=int, default=15)
+    ap.add_argument("--learned-heldout", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--dslash-only", action="store_true", help="time the hop kernel alone (profiling aid)")
     ap.add_argument("--dslash-lattice", type=int, nargs=2, default=(32, 24), metavar=("L", "T"))

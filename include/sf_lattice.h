@@ -97,7 +97,7 @@ typedef enum {
     SF_SOLVE_MIXED_DC = 1,
     /* FP64 defect correction around BiCGStab with FP16 hop operands */
     SF_SOLVE_MIXED_DC_HALF = 2,
-    /* FP64 flexible GCR (restarted, 8 directions) preconditioned by the
+    /* FP64 flexible GCR (restarted, 16 directions) preconditioned by the
        learned network attached with sf_lattice_set_preconditioner; the FP64
        true residual judges it, and FP32-inner BiCGStab under FP64 defect
        correction continues from its iterate if it stops above tol.  One

@@ -438,7 +438,7 @@ struct Workspace {
 
     // ---- flexible GCR (FP64) with the learned preconditioner
     struct Fgcr {
-        static constexpr int M = 8;
+        static constexpr int M = 16;
         int m = 0;
         FieldBuf z[M], w[M];
         FieldBuf r, g5a, g5b;
