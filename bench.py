@@ -74,6 +74,18 @@ def _ncu_traffic(key):
     return None
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The maximum of x over all ranks of the initialised process group (x on
+    a single process); every rank gets the result."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -183,11 +195,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), dev)
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
 
@@ -210,10 +218,7 @@ def run_ours(args, rank, world, local_rank):
         step(U_h, phi_h, X_h, Y_h, F_h, mom_h)
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dev)
     nb = lambda a: a.numel() * a.element_size()
     h2d = nb(U_h) + nb(phi_h) + nb(X_h) + nb(Y_h) + nb(mom_h)   # links, phi, X and Y into the force, mom
     d2h = nb(X_h) + nb(Y_h) + nb(F_h) + nb(mom_h)
