@@ -136,7 +136,10 @@ sf_status sf_lattice_set_links(sf_lattice* lat, const double* links);
 
 /* Fix the kernel tiling for one precision instead of autotuning it:
  * TS sites per tile (32, 64 or 128) and NR right-hand sides per thread
- * (1, 2, 3 or 5; FP64: 1 or 2).  TS = 0 restores autotuning. */
+ * (1, 2, 3 or 5; FP64: 1 or 2).  A block holds TS * ceil(nrhs / NR) threads,
+ * at most 256 (FP64, NR = 1), 128 (FP64, NR = 2), 320 / 384 / 256 (FP32 and
+ * FP16 with NR = 1 / 2 / 3 or 5): checked when a solve or apply uses the
+ * tiling, SF_EINVAL beyond.  TS = 0 restores autotuning. */
 sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR);
 
 /* Tiling in use for a precision and block size (runs the autotuner if it has

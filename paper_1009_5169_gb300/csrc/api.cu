@@ -196,6 +196,20 @@ struct sf_lattice {
 };
 
 // ---------------------------------------------------------------- workspace
+// Tilings the kernels of a precision index (0 FP64, 1 FP32, 2 FP16 hop
+// operands, 3 FP64 vector kernels) are compiled for: blocks of TS sites x
+// ceil(nrhs / NR) right-hand-side groups within the kernels' launch bounds
+// (FP64: NR = 1 or 2; FP32 / FP16: NR = 1, 2, 3 or 5).
+inline bool tiling_ok(int ci, int TS, int NR, int nrhs) {
+    const int threads = TS * ((nrhs + NR - 1) / NR);
+    if (ci == 1 || ci == 2) {
+        if (NR != 1 && NR != 2 && NR != 3 && NR != 5) return false;
+        return threads <= (NR == 1 ? 320 : NR == 2 ? 384 : 256);
+    }
+    if (NR != 1 && NR != 2) return false;
+    return threads <= (NR == 1 ? 256 : 128);
+}
+
 struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -229,7 +243,7 @@ struct Workspace {
         bool ok = false;
     } inner[3];
 
-    DevMem st, ost, partials, counters, loop_count, nrm_bb, nrm_rr, n_active;
+    DevMem st, ost, partials, loop_count, nrm_bb, nrm_rr, n_active;
     DevMem io;   // canonical AoS staging for batched pack/unpack
     DevMem aux;  // per-rhs scalars of the learned preconditioner's training
     int* pin = nullptr;  // pinned: [0] n_active, [1] loop_count
@@ -272,9 +286,8 @@ struct Workspace {
             const int L3h = ls[l]->L * ls[l]->L * ls[l]->L / 2;
             maxblk += std::min(((L3h + 31) / 32) * (ls[l]->T - 1), 8 * sm_count);
         }
+        // per-block partial sums of the reductions (3 rows per rhs at most)
         partials.ensure((size_t)3 * nrhs * maxblk * sizeof(double));
-        counters.ensure((size_t)nlat * sizeof(unsigned));
-        CK(cudaMemset(counters.p, 0, (size_t)nlat * sizeof(unsigned)));
         loop_count.ensure(4 * sizeof(int));  // [0] WHILE iterations, [1] cap, [2] continue flag
         nrm_bb.ensure(n * sizeof(double));
         nrm_rr.ensure(n * sizeof(double));
@@ -336,7 +349,6 @@ struct Workspace {
         c.st = with_state ? st.as<KState>() : nullptr;
         c.ost = ost.as<OState>();
         c.partials = partials.as<double>();
-        c.counters = counters.as<unsigned>();
         c.loop_count = loop_count.as<int>();
         c.cond = 0;
         c.use_cond = 0;
@@ -347,7 +359,7 @@ struct Workspace {
         return hop_prec(ci) == vec_prec(ci) ? vec.ptr() : copy.ptr();
     }
 
-    // one BiCGStab iteration on all rhs (7 kernels)
+    // one BiCGStab iteration on all rhs: 7 kernels and the lattice sums of its 3 reductions
     void enqueue_iteration(int ci, bool dag, const SolverCtx& k, cudaStream_t s) {
         const KrylovOps& o = ops_for(ci);
         const LaunchCfg& lc = cfg[ci].lc;
@@ -410,7 +422,10 @@ struct Workspace {
         }
         // explicit tiling of the (single) lattice wins
         if (nlat == 1 && lats[0]->tune_TS[ci] > 0) {
-            set_tiling(ci, lats[0]->tune_TS[ci], lats[0]->tune_NR[ci]);
+            const int TS = lats[0]->tune_TS[ci], NR = lats[0]->tune_NR[ci];
+            REQUIRE(tiling_ok(ci, TS, NR, nrhs),
+                    "tiling exceeds the block size of this precision (TS * ceil(nrhs / NR) threads)");
+            set_tiling(ci, TS, NR);
             return;
         }
         autotune(ci);
@@ -425,7 +440,7 @@ struct Workspace {
         CK(o.hop(lc, 1, dag, x.ptr(), t64o.ptr(), 1.0, 0, nullptr, s));
         CK(o.tail(lc, 0, dag, RED_NORM, t64o.ptr(), x.ptr(), phi.ptr(), r64.ptr(), FieldPtr{nullptr, nullptr}, -1.0,
                   1.0, 2, &k, nrm_rr.as<double>(), s));
-        launches += 2;
+        launches += 3;  // hop, tail, lattice sums
     }
 
     // The full FP64-outer / inner-precision solve of Dhat x = phi (dag: Dhat^dag).
@@ -459,7 +474,7 @@ struct Workspace {
     void dots64(const FieldBuf& a, const FieldBuf& b, double2* dev_out, cudaStream_t s) {
         SolverCtx k = ctx(false);
         CK(launch_dot64(cfg[3].lc, a.ptr(), b.ptr(), &k, dev_out, s));
-        launches += 1;
+        launches += 2;
     }
 
     Result fgcr(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
@@ -483,7 +498,7 @@ struct Workspace {
         if (!from_x) CK(cudaMemsetAsync(x.v.p, 0, field_bytes(Prec::F64, S), s));
         SolverCtx k0 = ctx(false);
         CK(launch_norm2(cfg[0].lc, phi.ptr(), &k0, nrm_bb.as<double>(), s));
-        launches += 1;
+        launches += 2;
         GraphEntry& ge = graph(ci, dag);
         pin[2] = maxiter + 8;
         CK(cudaMemcpyAsync(loop_count.as<int>() + 1, pin + 2, sizeof(int), cudaMemcpyHostToDevice, s));
@@ -521,9 +536,9 @@ struct Workspace {
             }
             CK(o.dc_update(cfg[ci].lc, x.ptr(), inner[ci].x.ptr(), &k, s));
             CK(cudaMemcpyAsync(pin + 1, loop_count.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-            launches += 2;
+            launches += 3;  // init (+ its sums), dc_update
             CK(cudaStreamSynchronize(s));
-            launches += 7LL * pin[1];
+            launches += 10LL * pin[1];  // kernels of one iteration
         }
         std::vector<OState> out(n);
         CK(cudaMemcpy(out.data(), ost.p, n * sizeof(OState), cudaMemcpyDeviceToHost));
@@ -553,11 +568,6 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 
-int maxt(int ci, int NR) {
-    if (ci == 0) return NR == 1 ? 256 : 128;
-    return NR == 1 ? 320 : NR == 2 ? 384 : 256;
-}
-
 }  // namespace
 
 void Workspace::autotune(int ci) {
@@ -585,11 +595,9 @@ void Workspace::autotune(int ci) {
     int bTS = 64, bNR = 1;
     const FieldPtr none{nullptr, nullptr};
     for (int NR : nrs_all) {
-        if (ci == 0 && NR > 2) continue;
         if (NR > nrhs) continue;
-        const int RG = (nrhs + NR - 1) / NR;
         for (int TS : tss) {
-            if (TS * RG > maxt(ci, NR)) continue;
+            if (!tiling_ok(ci, TS, NR, nrhs)) continue;
             set_tiling(ci, TS, NR);
             const LaunchCfg& lc = cfg[ci].lc;
             Inner& in = inner[ci];

@@ -345,10 +345,10 @@ cudaError_t launch_outer_check(int n, OState* ost, const double* rr, const doubl
     return cudaGetLastError();
 }
 
+// |f_i|^2 per (lattice, rhs): block partials here, the sums by k_finish
 template <int NR>
 __global__ void __launch_bounds__(KB<P64, NR>::MAXT, KB<P64, NR>::MINB) k_norm2(const LatDev* __restrict__ lats, int nlat, int nrhs,
-                                                CField<P64> f, SolverCtx ctx, double* __restrict__ out) {
-    __shared__ double sres[MAX_RHS * 3];
+                                                CField<P64> f, SolverCtx ctx) {
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y * NR;
@@ -367,27 +367,24 @@ __global__ void __launch_bounds__(KB<P64, NR>::MAXT, KB<P64, NR>::MINB) k_norm2(
             norm_acc(a, red[j][0]);
         }
     }
-    if (!reduce_lattice<NR, 1>(red, nrhs, l, g, ctx.partials, ctx.counters, sres)) return;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if (tid < nrhs) out[l * nrhs + tid] = sres[tid];
+    block_partials<NR, 1>(red, nrhs, ctx.partials);
 }
 
 cudaError_t launch_norm2(const LaunchCfg& c, FieldPtr f, const SolverCtx* ctx, double* out, cudaStream_t st) {
     if (c.NR == 1)
-        k_norm2<1><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(f), *ctx, out);
+        k_norm2<1><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(f), *ctx);
     else if (c.NR == 2)
-        k_norm2<2><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(f), *ctx, out);
+        k_norm2<2><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(f), *ctx);
     else
         return cudaErrorInvalidValue;
+    launch_finish<1, double, FIN_NORM, double>(c, *ctx, out, 0, st);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ FP64 BLAS for FGCR
 // out[l*nrhs + i] = <a_i, b_i> (complex, sum conj(a) b) for every (lattice, rhs)
 __global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_dot64(const LatDev* __restrict__ lats, int nlat, int nrhs,
-                                                          CField<P64> a, CField<P64> b, SolverCtx ctx,
-                                                          double2* __restrict__ out) {
-    __shared__ double sres[MAX_RHS * 3];
+                                                          CField<P64> a, CField<P64> b, SolverCtx ctx) {
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y;
@@ -402,9 +399,7 @@ __global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_dot64(const LatDev* __rest
             dotc_acc(x, y, red[0][0], red[0][1]);
         }
     }
-    if (!reduce_lattice<1, 2>(red, nrhs, l, g, ctx.partials, ctx.counters, sres)) return;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if (tid < nrhs) out[l * nrhs + tid] = make_double2(sres[tid * 2], sres[tid * 2 + 1]);
+    block_partials<1, 2>(red, nrhs, ctx.partials);
 }
 
 // y_i += sum_j c[j][i] x_j for nvec vectors x_j (coefficients per rhs, device)
@@ -447,7 +442,8 @@ __global__ void k_gamma5_64(long long n_per_rhs_planes, int Vpad, const double2*
 
 cudaError_t launch_dot64(const LaunchCfg& c, FieldPtr a, FieldPtr b, const SolverCtx* ctx, double2* out,
                          cudaStream_t st) {
-    k_dot64<<<c.nblocks, dim3(c.TS, c.nrhs), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(a), cf<P64>(b), *ctx, out);
+    k_dot64<<<c.nblocks, dim3(c.TS, c.nrhs), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(a), cf<P64>(b), *ctx);
+    launch_finish<2, double, FIN_DOT, double>(c, *ctx, reinterpret_cast<double*>(out), 0, st);
     return cudaGetLastError();
 }
 

@@ -119,15 +119,54 @@ __device__ __forceinline__ void hop_site(const LatDev& g, const SiteX& s, int cb
 constexpr int MAX_WARPS = 32;
 constexpr int MAX_RHS = 16;
 
-// Block-reduce vals[j][q] (rhs = threadIdx.y * NR + j), publish per-block
-// partials, and in the lattice's last block sum them in block order into
-// sres[rhs * NQ + q].  Returns true in that last block.  Every thread of the
-// block must call it.
-template <int NR, int NQ>
-__device__ bool reduce_lattice(const double (&vals)[NR][NQ], int nrhs, int l, const LatDev& g,
-                               double* __restrict__ partials, unsigned* __restrict__ counters, double* sres) {
-    __shared__ double sw[MAX_WARPS][NR][NQ];
-    __shared__ int is_last;
+// Reduction accumulators.  FP64 fields reduce in double.  The FP32 / FP16
+// solver reduces in float-float (an unevaluated sum hi + lo of two floats,
+// combined with Knuth's error-free TwoSum), about 44 significant bits: the
+// FP64 pipe of this GPU retires a small fraction of the FP32 rate, and a
+// double shuffle tree per warp would cost more than the kernel's memory
+// traffic.  Results leave the reduction as double.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff acc_add(ff a, ff b) {
+    const float s = __fadd_rn(a.hi, b.hi);  // TwoSum: s + e = a.hi + b.hi exactly
+    const float bv = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+    const float lo = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, lo);  // renormalise (FastTwoSum, |s| >= |lo|)
+    return ff{h, __fsub_rn(lo, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ ff acc_shfl_down(ff v, int off) {
+    return ff{__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+}
+__device__ __forceinline__ double acc_shfl_down(double v, int off) { return __shfl_down_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ double acc_to_double(ff v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ double acc_to_double(double v) { return v; }
+__device__ __forceinline__ ff acc_ldcg(const ff* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return ff{v.x, v.y};
+}
+__device__ __forceinline__ double acc_ldcg(const double* p) { return __ldcg(p); }
+template <typename A> __device__ __forceinline__ A acc_zero() { return A{}; }
+__device__ __forceinline__ void store_acc(ff* p, ff v) { *p = v; }
+__device__ __forceinline__ void store_acc(double* p, double v) { *p = v; }
+__device__ __forceinline__ void store_acc(double* p, ff v) { *p = acc_to_double(v); }
+template <typename R> struct AccOf { using T = double; };
+template <> struct AccOf<float> { using T = ff; };
+
+// Per-block partial sums: vals[j][q] of every thread (rhs = threadIdx.y * NR
+// + j) -> partials[(rhs * NQ + q) * gridDim.x + blockIdx.x], a fixed shuffle
+// tree per warp and a fixed sum over the warps of a rhs group.  Every thread
+// of the block calls it.  The lattice sums are formed by k_finish, launched
+// next on the same stream: the kernel boundary orders the partials, where a
+// last-block-done scheme inside the kernel pays device-scope fences on every
+// block's critical path.
+template <int NR, int NQ, typename A>
+__device__ __forceinline__ void block_partials(const A (&vals)[NR][NQ], int nrhs, double* __restrict__ partials_) {
+    static_assert(sizeof(A) == sizeof(double), "partials hold 8-byte accumulators");
+    A* __restrict__ partials = reinterpret_cast<A*>(partials_);
+    __shared__ A sw[MAX_WARPS][NR][NQ];
     const int lane = threadIdx.x & 31;
     const int wpr = blockDim.x >> 5;
     const int w = threadIdx.y * wpr + (threadIdx.x >> 5);
@@ -135,9 +174,9 @@ __device__ bool reduce_lattice(const double (&vals)[NR][NQ], int nrhs, int l, co
     for (int j = 0; j < NR; ++j)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            double v = vals[j][q];
+            A v = vals[j][q];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            for (int off = 16; off > 0; off >>= 1) v = acc_add(v, acc_shfl_down(v, off));
             if (lane == 0) sw[w][j][q] = v;
         }
     __syncthreads();
@@ -146,35 +185,179 @@ __device__ bool reduce_lattice(const double (&vals)[NR][NQ], int nrhs, int l, co
         const int y = tid / (NR * NQ), jq = tid % (NR * NQ), j = jq / NQ, q = jq % NQ;
         const int rhs = y * NR + j;
         if (rhs < nrhs) {
-            double s = 0.0;
-            for (int k = 0; k < wpr; ++k) s += sw[y * wpr + k][j][q];
+            A s = acc_zero<A>();
+            for (int k = 0; k < wpr; ++k) s = acc_add(s, sw[y * wpr + k][j][q]);
             partials[(long long)(rhs * NQ + q) * gridDim.x + blockIdx.x] = s;
         }
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        const unsigned prev = atomicAdd(&counters[l], 1u);
-        is_last = (prev == (unsigned)(g.nblk - 1));
-    }
-    __syncthreads();
-    if (!is_last) return false;
-    __threadfence();
-    const int nw = (int)(blockDim.x * blockDim.y) >> 5;
-    for (int pr = tid >> 5; pr < nrhs * NQ; pr += nw) {
-        double s = 0.0;
-        for (int b = lane; b < g.nblk; b += 32) s += __ldcg(partials + (long long)pr * gridDim.x + g.blk0 + b);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (lane == 0) sres[pr] = s;
-    }
-    __syncthreads();
-    if (tid == 0) counters[l] = 0u;
-    return true;
 }
 
-template <typename R>
-__device__ __forceinline__ void dotc_acc(const cpx<R> (&a)[4][3], const cpx<R> (&b)[4][3], double& re, double& im) {
+// ------------------------------------------------------------ coefficients
+// BiCGStab scalars alpha = rho / <r0, v>, omega = <t, s> / |t|^2,
+// beta = (rho' / rho)(alpha / omega).  The FP64 solver forms them in double.
+// The FP32 inner solver forms them in float from the double sums: they only
+// scale FP32 vectors, and one thread's double complex divisions on this GPU's
+// narrow FP64 pipe take microseconds per iteration.  KState keeps both forms.
+__device__ __forceinline__ float2 f2of(double2 a) { return make_float2((float)a.x, (float)a.y); }
+// a / b by Smith's scaled algorithm (no overflow of |b|^2)
+__device__ __forceinline__ float2 cdivf(float2 a, float2 b) {
+    if (fabsf(b.x) >= fabsf(b.y)) {
+        const float r = b.y / b.x, d = b.x + r * b.y;
+        return make_float2((a.x + r * a.y) / d, (a.y - r * a.x) / d);
+    }
+    const float r = b.x / b.y, d = b.y + r * b.x;
+    return make_float2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+}
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 d2of(float2 a) { return make_double2((double)a.x, (double)a.y); }
+
+template <typename RV> struct Coef;
+template <>
+struct Coef<double> {
+    static __device__ __forceinline__ cpx<double> alpha(const KState& k) { return cpx<double>{k.alpha.x, k.alpha.y}; }
+    static __device__ __forceinline__ cpx<double> omega(const KState& k) { return cpx<double>{k.omega.x, k.omega.y}; }
+    static __device__ __forceinline__ cpx<double> beta(const KState& k) { return cpx<double>{k.beta.x, k.beta.y}; }
+    static __device__ __forceinline__ void set_alpha(KState& k, double2 r0v) { k.alpha = cdiv(k.rho, r0v); }
+    static __device__ __forceinline__ void set_omega(KState& k, double2 ts, double tt) {
+        k.omega = make_double2(ts.x / tt, ts.y / tt);
+    }
+    static __device__ __forceinline__ void set_beta(KState& k, double2 rho_new) {
+        k.beta = cmul(cdiv(rho_new, k.rho), cdiv(k.alpha, k.omega));
+    }
+};
+template <>
+struct Coef<float> {
+    static __device__ __forceinline__ cpx<float> alpha(const KState& k) { return cpx<float>{k.alpha_f.x, k.alpha_f.y}; }
+    static __device__ __forceinline__ cpx<float> omega(const KState& k) { return cpx<float>{k.omega_f.x, k.omega_f.y}; }
+    static __device__ __forceinline__ cpx<float> beta(const KState& k) { return cpx<float>{k.beta_f.x, k.beta_f.y}; }
+    static __device__ __forceinline__ void set_alpha(KState& k, double2 r0v) {
+        k.alpha_f = cdivf(f2of(k.rho), f2of(r0v));
+        k.alpha = d2of(k.alpha_f);
+    }
+    static __device__ __forceinline__ void set_omega(KState& k, double2 ts, double tt) {
+        const float t = (float)tt;
+        k.omega_f = make_float2((float)ts.x / t, (float)ts.y / t);
+        k.omega = d2of(k.omega_f);
+    }
+    static __device__ __forceinline__ void set_beta(KState& k, double2 rho_new) {
+        k.beta_f = cmulf(cdivf(f2of(rho_new), f2of(k.rho)), cdivf(k.alpha_f, k.omega_f));
+        k.beta = d2of(k.beta_f);
+    }
+};
+
+// What k_finish does with the lattice sums of a reduction.
+enum FinMode {
+    FIN_R0V = 0,   // alpha = rho / <r0, v>
+    FIN_TS = 1,    // omega = <t, s> / |t|^2
+    FIN_XR = 2,    // rho', |r|^2, beta, iteration count and convergence
+    FIN_INIT = 3,  // inner-solve start from |b|^2
+    FIN_NORM = 4,  // out[i] = sum
+    FIN_DOT = 5,   // ((double2*) out)[i] = (re, im)
+};
+constexpr int FIN_THREADS = 512;
+
+// Sum the block partials of each lattice (block l of this launch: rows
+// rhs * NQ + q over the lattice's blocks blk0 .. blk0 + nblk - 1, lane k
+// taking blocks k, k + 32, ... in batches of eight independent loads, then a
+// shuffle tree: a fixed order) and apply MODE for each rhs.
+template <int NQ, typename A, int MODE, typename RV>
+__global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict__ lats, int nrhs, int nblocks,
+                                                         SolverCtx ctx, double* __restrict__ out, int maxiter) {
+    __shared__ double sres[MAX_RHS * 3];
+    const int l = blockIdx.x;
+    const int blk0 = lats[l].blk0, nblk = lats[l].nblk;
+    const A* __restrict__ partials = reinterpret_cast<const A*>(ctx.partials);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = (int)blockDim.x >> 5;
+    for (int r = w; r < nrhs * NQ; r += nw) {
+        const A* src = partials + (long long)r * nblocks + blk0;
+        A a = acc_zero<A>();
+        for (int c0 = 0; c0 < nblk; c0 += 32 * 8) {
+            A v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int c = c0 + 32 * k + lane;
+                v[k] = (c < nblk) ? acc_ldcg(src + c) : acc_zero<A>();
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a = acc_add(a, v[k]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a = acc_add(a, acc_shfl_down(a, off));
+        if (lane == 0) sres[r] = acc_to_double(a);
+    }
+    __syncthreads();
+    if (MODE == FIN_INIT && l == 0 && tid == 0) *ctx.loop_count = 0;
+    if (tid >= nrhs) return;
+    const int i = l * nrhs + tid;
+    if (MODE == FIN_NORM) {
+        out[i] = sres[tid];
+        return;
+    }
+    if (MODE == FIN_DOT) {
+        reinterpret_cast<double2*>(out)[i] = make_double2(sres[2 * tid], sres[2 * tid + 1]);
+        return;
+    }
+    KState& st = ctx.st[i];
+    if (MODE == FIN_INIT) {
+        const OState& o = ctx.ost[i];
+        st.rho = make_double2(sres[tid], 0.0);
+        st.rr = sres[tid];
+        st.alpha = make_double2(1.0, 0.0);
+        st.omega = make_double2(1.0, 0.0);
+        st.beta = make_double2(0.0, 0.0);
+        st.alpha_f = make_float2(1.f, 0.f);
+        st.omega_f = make_float2(1.f, 0.f);
+        st.beta_f = make_float2(0.f, 0.f);
+        st.iters = 0;
+        st.maxiter = maxiter;
+        st.flags = 0;
+        st.target2 = o.delta2;
+        st.active = (o.active && sres[tid] > o.delta2) ? 1 : 0;
+        return;
+    }
+    if (!st.active) return;
+    if (MODE == FIN_R0V) {
+        const double2 r0v = make_double2(sres[2 * tid], sres[2 * tid + 1]);
+        if (r0v.x == 0.0 && r0v.y == 0.0) {
+            st.active = 0;
+            st.flags |= 1;
+        } else {
+            Coef<RV>::set_alpha(st, r0v);
+        }
+    } else if (MODE == FIN_TS) {
+        const double2 ts = make_double2(sres[3 * tid], sres[3 * tid + 1]);
+        const double tt = sres[3 * tid + 2];
+        if (tt > 0.0) {
+            Coef<RV>::set_omega(st, ts, tt);
+        } else {
+            st.omega = make_double2(0.0, 0.0);
+            st.omega_f = make_float2(0.f, 0.f);
+        }
+    } else if (MODE == FIN_XR) {
+        const double2 rho_new = make_double2(sres[3 * tid], sres[3 * tid + 1]);
+        const double rr = sres[3 * tid + 2];
+        st.rr = rr;
+        st.iters += 1;
+        const bool om0 = (st.omega.x == 0.0 && st.omega.y == 0.0);
+        const bool rho0 = (rho_new.x == 0.0 && rho_new.y == 0.0);
+        if (!om0 && !rho0) Coef<RV>::set_beta(st, rho_new);
+        st.rho = rho_new;
+        if (om0) st.flags |= 2;
+        if (rho0) st.flags |= 1;
+        const bool go = (rr > st.target2) && (st.iters < st.maxiter) && !om0 && !rho0;
+        st.active = go ? 1 : 0;
+    }
+}
+
+template <int NQ, typename A, int MODE, typename RV>
+inline void launch_finish(const LaunchCfg& c, const SolverCtx& ctx, double* out, int maxiter, cudaStream_t st) {
+    k_finish<NQ, A, MODE, RV><<<c.nlat, FIN_THREADS, 0, st>>>(c.lats, c.nrhs, c.nblocks, ctx, out, maxiter);
+}
+
+template <typename R, typename A>
+__device__ __forceinline__ void dotc_acc(const cpx<R> (&a)[4][3], const cpx<R> (&b)[4][3], A& re, A& im) {
     R sr = 0, si = 0;
 #pragma unroll
     for (int s = 0; s < 4; ++s)
@@ -185,11 +368,11 @@ __device__ __forceinline__ void dotc_acc(const cpx<R> (&a)[4][3], const cpx<R> (
             si = fma(a[s][c].re, b[s][c].im, si);
             si = fma(-a[s][c].im, b[s][c].re, si);
         }
-    re += (double)sr;
-    im += (double)si;
+    re = acc_add(re, A{sr});
+    im = acc_add(im, A{si});
 }
-template <typename R>
-__device__ __forceinline__ void norm_acc(const cpx<R> (&a)[4][3], double& n) {
+template <typename R, typename A>
+__device__ __forceinline__ void norm_acc(const cpx<R> (&a)[4][3], A& n) {
     R s = 0;
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp)
@@ -198,7 +381,7 @@ __device__ __forceinline__ void norm_acc(const cpx<R> (&a)[4][3], double& n) {
             s = fma(a[sp][c].re, a[sp][c].re, s);
             s = fma(a[sp][c].im, a[sp][c].im, s);
         }
-    n += (double)s;
+    n = acc_add(n, A{s});
 }
 
 __device__ __forceinline__ bool rhs_active(const KState* st, int idx) { return st == nullptr || st[idx].active != 0; }
@@ -244,11 +427,10 @@ template <typename PH, typename PV, int NR, bool DAG, int RED, bool HASZ>
 __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_tail(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
                                                CField<PH> hin, CField<PV> xv, CField<PV> zv, Field<PV> out,
                                                CField<PV> ra, double a, double coef, int kpow,
-                                               SolverCtx ctx, double* __restrict__ norm_out) {
+                                               SolverCtx ctx) {
     using RH = typename PH::real;
     using RV = typename PV::real;
     constexpr int NQ = (RED == RED_TS) ? 3 : (RED == RED_R0V) ? 2 : 1;
-    __shared__ double sres[MAX_RHS * 3];
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y * NR;
@@ -260,11 +442,12 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_tail(con
         act[j] = (j < nval) && rhs_active(ctx.st, l * nrhs + r0 + j);
         any = any || act[j];
     }
-    double red[NR][NQ];
+    using A = typename AccOf<RV>::T;
+    A red[NR][NQ];
 #pragma unroll
     for (int j = 0; j < NR; ++j)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) red[j][q] = 0.0;
+        for (int q = 0; q < NQ; ++q) red[j][q] = acc_zero<A>();
     const RV av = (RV)a;
     const RV cv = (RV)(coef * (kpow == 0 ? 1.0 : kpow == 1 ? g.kappa : g.kappa * g.kappa));
     if (any) {
@@ -308,33 +491,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_tail(con
         }
     }
     if (RED == RED_NONE) return;
-    if (!reduce_lattice<NR, NQ>(red, nrhs, l, g, ctx.partials, ctx.counters, sres)) return;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if (tid < nrhs) {
-        const int i = l * nrhs + tid;
-        if (RED == RED_NORM) {
-            norm_out[i] = sres[tid];
-        } else if (ctx.st != nullptr && ctx.st[i].active) {
-            KState& st = ctx.st[i];
-            if (RED == RED_R0V) {
-                const double2 r0v = make_double2(sres[tid * NQ], sres[tid * NQ + (NQ > 1 ? 1 : 0)]);
-                if (r0v.x == 0.0 && r0v.y == 0.0) {
-                    st.active = 0;
-                    st.flags |= 1;
-                } else {
-                    st.alpha = cdiv(st.rho, r0v);
-                }
-            } else if (RED == RED_TS) {
-                const double2 ts = make_double2(sres[tid * NQ], sres[tid * NQ + (NQ > 1 ? 1 : 0)]);
-                const double tt = sres[tid * NQ + (NQ > 2 ? 2 : 0)];
-                if (tt > 0.0) {
-                    st.omega = make_double2(ts.x / tt, ts.y / tt);
-                } else {
-                    st.omega = make_double2(0.0, 0.0);
-                }
-            }
-        }
-    }
+    block_partials<NR, NQ>(red, nrhs, ctx.partials);
 }
 
 // s = r - alpha v (and its hop-precision copy)
@@ -356,7 +513,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_s_update
             if (j >= nval) continue;
             const KState& k = st[l * nrhs + r0 + j];
             if (!k.active) continue;
-            const cpx<RV> al = cpx<RV>{(RV)k.alpha.x, (RV)k.alpha.y};
+            const cpx<RV> al = Coef<RV>::alpha(k);
             cpx<RV> a[4][3], b[4][3];
             load_spinor<PV, RV>(r, vbase<PV>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), a);
             load_spinor<PV, RV>(v, vbase<PV>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), b);
@@ -376,22 +533,22 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_xr_updat
                                                     Field<PV> x, Field<PV> r, CField<PV> p, CField<PV> s,
                                                     CField<PV> t, CField<PV> r0f, SolverCtx ctx) {
     using RV = typename PV::real;
-    __shared__ double sres[MAX_RHS * 3];
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y * NR;
     const int nval = min(NR, nrhs - r0);
-    double red[NR][3];
+    using A = typename AccOf<RV>::T;
+    A red[NR][3];
     bool act[NR];
     cpx<RV> al[NR], om[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-        red[j][0] = red[j][1] = red[j][2] = 0.0;
+        red[j][0] = red[j][1] = red[j][2] = acc_zero<A>();
         act[j] = (j < nval) && ctx.st[l * nrhs + r0 + j].active;
         if (act[j]) {
             const KState& k = ctx.st[l * nrhs + r0 + j];
-            al[j] = cpx<RV>{(RV)k.alpha.x, (RV)k.alpha.y};
-            om[j] = cpx<RV>{(RV)k.omega.x, (RV)k.omega.y};
+            al[j] = Coef<RV>::alpha(k);
+            om[j] = Coef<RV>::omega(k);
         }
     }
     for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
@@ -421,25 +578,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_xr_updat
             norm_acc(sa, red[j][2]);
         }
     }
-    if (!reduce_lattice<NR, 3>(red, nrhs, l, g, ctx.partials, ctx.counters, sres)) return;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if (tid < nrhs) {
-        KState& st = ctx.st[l * nrhs + tid];
-        if (st.active) {
-            const double2 rho_new = make_double2(sres[tid * 3], sres[tid * 3 + 1]);
-            const double rr = sres[tid * 3 + 2];
-            st.rr = rr;
-            st.iters += 1;
-            const bool om0 = (st.omega.x == 0.0 && st.omega.y == 0.0);
-            const bool rho0 = (rho_new.x == 0.0 && rho_new.y == 0.0);
-            if (!om0 && !rho0) st.beta = cmul(cdiv(rho_new, st.rho), cdiv(st.alpha, st.omega));
-            st.rho = rho_new;
-            if (om0) st.flags |= 2;
-            if (rho0) st.flags |= 1;
-            const bool go = (rr > st.target2) && (st.iters < st.maxiter) && !om0 && !rho0;
-            st.active = go ? 1 : 0;
-        }
-    }
+    block_partials<NR, 3>(red, nrhs, ctx.partials);
 }
 
 // p = r + beta (p - omega v); the first block also drives the WHILE node
@@ -461,8 +600,8 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_p_update
             if (j >= nval) continue;
             const KState& k = ctx.st[l * nrhs + r0 + j];
             if (!k.active) continue;
-            const cpx<RV> be = cpx<RV>{(RV)k.beta.x, (RV)k.beta.y};
-            const cpx<RV> om = cpx<RV>{(RV)k.omega.x, (RV)k.omega.y};
+            const cpx<RV> be = Coef<RV>::beta(k);
+            const cpx<RV> om = Coef<RV>::omega(k);
             const long long vb = vbase<PV>(g, r0 + j), sb = sbase(g, r0 + j);
             cpx<RV> pa[4][3], ra[4][3], va[4][3];
             load_spinor<PV, RV>(CField<PV>{p.v, p.scale}, vb, g.Vpad, cb, sb, pa);
@@ -490,20 +629,20 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_p_update
 template <typename PV, typename PH, int NR>
 __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_inner_init(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                      CField<P64> r64, Field<PV> x, Field<PV> r, Field<PV> r0f,
-                                                     Field<PV> p, Field<PH> ph, SolverCtx ctx, int maxiter) {
+                                                     Field<PV> p, Field<PH> ph, SolverCtx ctx) {
     using RV = typename PV::real;
     constexpr bool COPY = !std::is_same<PV, PH>::value;
-    __shared__ double sres[MAX_RHS * 3];
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y * NR;
     const int nval = min(NR, nrhs - r0);
-    double red[NR][1];
+    using A = typename AccOf<RV>::T;
+    A red[NR][1];
     bool act[NR];
     double inv[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-        red[j][0] = 0.0;
+        red[j][0] = acc_zero<A>();
         act[j] = (j < nval) && ctx.ost[l * nrhs + r0 + j].active;
         inv[j] = act[j] ? ctx.ost[l * nrhs + r0 + j].inv_norm : 0.0;
     }
@@ -533,24 +672,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_inner_in
             norm_acc(b, red[j][0]);
         }
     }
-    if (!reduce_lattice<NR, 1>(red, nrhs, l, g, ctx.partials, ctx.counters, sres)) return;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if (tid < nrhs) {
-        const int i = l * nrhs + tid;
-        KState& st = ctx.st[i];
-        const OState& o = ctx.ost[i];
-        st.rho = make_double2(sres[tid], 0.0);
-        st.rr = sres[tid];
-        st.alpha = make_double2(1.0, 0.0);
-        st.omega = make_double2(1.0, 0.0);
-        st.beta = make_double2(0.0, 0.0);
-        st.iters = 0;
-        st.maxiter = maxiter;
-        st.flags = 0;
-        st.target2 = o.delta2;
-        st.active = (o.active && sres[tid] > o.delta2) ? 1 : 0;
-    }
-    if (tid == 0) *ctx.loop_count = 0;
+    block_partials<NR, 1>(red, nrhs, ctx.partials);
 }
 
 // x64 += x / inv_norm for the rhs that iterated in this sweep
@@ -666,12 +788,23 @@ struct OpsImpl {
 #define SF_TAIL(RED, HZ)                                                                              \
     k_tail<PH, PV, NR, DAG, RED, HZ><<<c.nblocks, b, 0, st>>>(c.lats, c.nlat, c.nrhs, out_par, cf<PH>(hin), \
                                                               cf<PV>(xv), cf<PV>(zv), wf<PV>(out), cf<PV>(ra), \
-                                                              a, coef, kpow, k, norm_out)
+                                                              a, coef, kpow, k)
+        using A = typename AccOf<typename PV::real>::T;
+        using RV = typename PV::real;
         switch (red) {
             case RED_NONE: if (hz) SF_TAIL(RED_NONE, true); else SF_TAIL(RED_NONE, false); break;
-            case RED_R0V: SF_TAIL(RED_R0V, false); break;
-            case RED_TS: SF_TAIL(RED_TS, false); break;
-            case RED_NORM: if (hz) SF_TAIL(RED_NORM, true); else SF_TAIL(RED_NORM, false); break;
+            case RED_R0V:
+                SF_TAIL(RED_R0V, false);
+                launch_finish<2, A, FIN_R0V, RV>(c, k, nullptr, 0, st);
+                break;
+            case RED_TS:
+                SF_TAIL(RED_TS, false);
+                launch_finish<3, A, FIN_TS, RV>(c, k, nullptr, 0, st);
+                break;
+            case RED_NORM:
+                if (hz) SF_TAIL(RED_NORM, true); else SF_TAIL(RED_NORM, false);
+                launch_finish<1, A, FIN_NORM, RV>(c, k, norm_out, 0, st);
+                break;
         }
 #undef SF_TAIL
     }
@@ -693,8 +826,10 @@ struct OpsImpl {
         SF_NR_SWITCH(c.NR, {
             k_inner_init<PV, PH, NR_><<<c.nblocks, block_of(c), 0, st>>>(
                 c.lats, c.nlat, c.nrhs, cf<P64>(r64), wf<PV>(x), wf<PV>(r), wf<PV>(r0), wf<PV>(p), wf<PH>(ph),
-                *ctx, maxiter);
+                *ctx);
         });
+        launch_finish<1, typename AccOf<typename PV::real>::T, FIN_INIT, typename PV::real>(c, *ctx, nullptr, maxiter,
+                                                                                           st);
         return cudaGetLastError();
     }
 
@@ -714,6 +849,7 @@ struct OpsImpl {
                                                                      cf<PV>(p), cf<PV>(s), cf<PV>(t), cf<PV>(r0),
                                                                      *ctx);
         });
+        launch_finish<3, typename AccOf<typename PV::real>::T, FIN_XR, typename PV::real>(c, *ctx, nullptr, 0, st);
         return cudaGetLastError();
     }
 

@@ -18,6 +18,7 @@ enum Red : int { RED_NONE = 0, RED_R0V = 1, RED_TS = 2, RED_NORM = 3 };
 // Per (lattice, rhs) state of one BiCGStab iteration, in device memory.
 struct KState {
     double2 rho, alpha, omega, beta;
+    float2 alpha_f, omega_f, beta_f;  // the same coefficients for the FP32 kernels
     double rr;        // |r|^2 of the iterated residual
     double target2;   // iterate while rr > target2
     int active;       // 1 while this rhs iterates
@@ -52,8 +53,7 @@ struct LaunchCfg {
 struct SolverCtx {
     KState* st;           // [nlat * nrhs]
     OState* ost;          // [nlat * nrhs]
-    double* partials;     // [NQmax * nrhs * nblocks]
-    unsigned* counters;   // [nlat], self-resetting
+    double* partials;     // [3 * nrhs * nblocks] per-block partial sums (k_finish adds them)
     int* loop_count;      // [0] iterations of the WHILE loop, [1] their cap, [2] continue flag
     cudaGraphConditionalHandle cond;
     int use_cond;

@@ -194,7 +194,7 @@ def test_rhs_independence_bitwise(sf):
     U = inputs.links(L, T, eps, 21)
     phi = inputs.sources(L, T, 3, 22)
     lat = sf.Lattice(L, T, theta, kappa, 4.52, torch.from_numpy(U).cuda())
-    lat.set_tuning("fp32", 64, 1)
+    lat.set_tuning("fp32", 32, 1)
     lat.set_tuning("fp64", 64, 1)
 
     def run(p):
@@ -253,4 +253,17 @@ def test_set_links_updates_every_precision(sf):
     for prec, tol in (("fp64", 1e-12), ("fp32", 2e-6), ("fp16", 4e-3)):
         sf.wilson_apply_block(lat, "dhat", prec, xd, out)
         assert relerr(out.cpu().numpy(), ref) <= tol, prec
+    lat.close()
+
+
+def test_tiling_validation(sf):
+    """Unsupported tilings are refused with SF_EINVAL, nothing launched."""
+    U, lat = _lattice(sf, 4, 4, 0.3, 0.125, 0.5)
+    for prec, TS, NR in (("fp32", 96, 1), ("fp16", 64, 4), ("fp64", 48, 1), ("fp64", 32, 3)):
+        with pytest.raises(sf.SFError):
+            lat.set_tuning(prec, TS, NR)
+    lat.set_tuning("fp64", 128, 2)   # 128 x 3 rhs groups > 128 threads at NR = 2
+    x = torch.from_numpy(inputs.sources(4, 4, 5, 3)).cuda()
+    with pytest.raises(sf.SFError):
+        sf.wilson_apply_block(lat, "dhat", "fp64", x, torch.empty_like(x))
     lat.close()
