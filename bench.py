@@ -60,13 +60,13 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(key):
-    """Per-launch DRAM bytes of the dslash kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def _ncu_traffic(key, TS, NR):
+    """Per-launch DRAM bytes of the dslash kernel at this tiling from the
+    committed ncu summary, if it was taken on the current kernel source."""
     try:
         with open(os.path.join(ROOT, "profiles", "dslash_traffic.json")) as f:
             d = json.load(f)
-        e = d.get(key)
+        e = d.get(f"{key}:TS{TS}NR{NR}")
         if e and e.get("kernel_hash") == _kernel_hash():
             return e
     except Exception:
@@ -252,7 +252,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_warm = a.elapsed_time(b) * 1e-3 / reps
     achieved = alg_bytes / t_cold / 1e9
-    tr = _ncu_traffic(f"{args.workload}:{prec}")
+    tr = _ncu_traffic(f"{args.workload}:{prec}", TS, NR)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "kernel": f"k_hop<{prec}> (dslash H_oe), TS={TS}, NR={NR}, L2 flushed before each launch",
@@ -291,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
             Vhb = Lh ** 3 * (Th - 1) // 2
             sb = {"fp32": nrhs * 96 * 2 + 8 * 48, "fp16": nrhs * 52 * 2 + 8 * 24}[p]
             ab = Vhb * sb
-            trb = _ncu_traffic(f"sf24:{p}")
+            trb = _ncu_traffic(f"sf24:{p}", TSb, NRb)
             res[p] = {"achieved": round(ab / t / 1e9, 1), "frac": round(ab / t / 1e9 / peak, 4),
                       "launch_us": round(t * 1e6, 2), "achieved_l2_flushed": round(ab / tc / 1e9, 1),
                       "launch_us_l2_flushed": round(tc * 1e6, 2), "algorithmic_bytes_per_launch": ab,

@@ -260,7 +260,7 @@ constexpr int FIN_THREADS = 512;
 
 // Sum the block partials of each lattice (block l of this launch: rows
 // rhs * NQ + q over the lattice's blocks blk0 .. blk0 + nblk - 1, lane k
-// taking blocks k, k + 32, ... in batches of eight independent loads, then a
+// taking blocks k, k + 32, ... in batches of 16 independent loads, then a
 // shuffle tree: a fixed order) and apply MODE for each rhs.
 template <int NQ, typename A, int MODE, typename RV>
 __global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict__ lats, int nrhs, int nblocks,
@@ -273,15 +273,15 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict
     for (int r = w; r < nrhs * NQ; r += nw) {
         const A* src = partials + (long long)r * nblocks + blk0;
         A a = acc_zero<A>();
-        for (int c0 = 0; c0 < nblk; c0 += 32 * 8) {
-            A v[8];
+        for (int c0 = 0; c0 < nblk; c0 += 32 * 16) {
+            A v[16];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < 16; ++k) {
                 const int c = c0 + 32 * k + lane;
                 v[k] = (c < nblk) ? acc_ldcg(src + c) : acc_zero<A>();
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) a = acc_add(a, v[k]);
+            for (int k = 0; k < 16; ++k) a = acc_add(a, v[k]);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) a = acc_add(a, acc_shfl_down(a, off));
