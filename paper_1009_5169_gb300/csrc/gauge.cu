@@ -15,6 +15,7 @@ namespace sf {
 // rounding.
 __global__ void k_link_prep(LatDev g, const double2* __restrict__ canon, double2* __restrict__ u64,
                             float4* __restrict__ u32, uint2* __restrict__ u16) {
+    pdl_enter();
     const int par = blockIdx.y;
     for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.Vh; cb += gridDim.x * blockDim.x) {
         const SiteX s = decode_site(g, cb, par);
@@ -48,7 +49,7 @@ __global__ void k_link_prep(LatDev g, const double2* __restrict__ canon, double2
 
 cudaError_t launch_link_prep(const LatDev& g, const double* canon, cudaStream_t st) {
     const int blocks = (g.Vh + 255) / 256;
-    k_link_prep<<<dim3(blocks < 1 ? 1 : blocks, 2), 256, 0, st>>>(
+    launch_pdl(k_link_prep, dim3(dim3(blocks < 1 ? 1 : blocks, 2)), dim3(256), st, 
         g, reinterpret_cast<const double2*>(canon), const_cast<double2*>(g.u64), const_cast<float4*>(g.u32),
         const_cast<uint2*>(g.u16));
     return cudaGetLastError();
@@ -58,6 +59,7 @@ cudaError_t launch_link_prep(const LatDev& g, const double* canon, cudaStream_t 
 // max over links of max_ij |(U^dag U - 1)_ij| and |det U - 1|, as the bit
 // patterns of non-negative doubles (atomicMax on them is order-preserving).
 __global__ void k_su3_check(int L, int T, const double2* __restrict__ canon, unsigned long long* out) {
+    pdl_enter();
     const long long L3 = (long long)L * L * L;
     const long long n = (long long)(T + 1) * L3 * 4;
     double e1 = 0.0, e2 = 0.0;
@@ -101,7 +103,7 @@ __global__ void k_su3_check(int L, int T, const double2* __restrict__ canon, uns
 cudaError_t launch_su3_check(int L, int T, const double* canon, unsigned long long* out2, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_su3_check<<<4 * 152, 256, 0, st>>>(L, T, reinterpret_cast<const double2*>(canon), out2);
+    launch_pdl(k_su3_check, dim3(4 * 152), dim3(256), st, L, T, reinterpret_cast<const double2*>(canon), out2);
     return cudaGetLastError();
 }
 
@@ -291,6 +293,7 @@ __device__ __forceinline__ void force_dir(const LatDev& g, const SiteX& s, int c
 __global__ void __launch_bounds__(128) k_force(const LatDev* __restrict__ lat, int nrhs, CField<P64> xe,
                                                CField<P64> xo, CField<P64> ye, CField<P64> yo, double* F,
                                                double* mom, double eps) {
+    pdl_enter();
     const LatDev g = *lat;
     const int par = blockIdx.y;
     const CField<P64> xs = par ? xo : xe, ys = par ? yo : ye;
@@ -310,7 +313,7 @@ cudaError_t launch_force(const LaunchCfg& c, FieldPtr xe, FieldPtr xo, FieldPtr 
     // grid is sized from the host copy passed through nblocks.
     int blocks = c.nblocks;
     if (blocks < 1) blocks = 1;
-    k_force<<<dim3(blocks, 2), 128, 0, st>>>(c.lats, c.nrhs, cf<P64>(xe), cf<P64>(xo), cf<P64>(ye), cf<P64>(yo),
+    launch_pdl(k_force, dim3(dim3(blocks, 2)), dim3(128), st, c.lats, c.nrhs, cf<P64>(xe), cf<P64>(xo), cf<P64>(ye), cf<P64>(yo),
                                              F, mom, eps);
     return cudaGetLastError();
 }
@@ -318,6 +321,7 @@ cudaError_t launch_force(const LaunchCfg& c, FieldPtr xe, FieldPtr xo, FieldPtr 
 // ------------------------------------------------------------ misc
 __global__ void k_outer_check(int n, OState* __restrict__ ost, const double* __restrict__ rr,
                               const double* __restrict__ bb, int max_sweeps, int* n_active) {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int cnt = 0;
     for (int i = 0; i < n; ++i) {
@@ -341,7 +345,7 @@ __global__ void k_outer_check(int n, OState* __restrict__ ost, const double* __r
 
 cudaError_t launch_outer_check(int n, OState* ost, const double* rr, const double* bb, int max_sweeps,
                                int* n_active, cudaStream_t st) {
-    k_outer_check<<<1, 32, 0, st>>>(n, ost, rr, bb, max_sweeps, n_active);
+    launch_pdl(k_outer_check, dim3(1), dim3(32), st, n, ost, rr, bb, max_sweeps, n_active);
     return cudaGetLastError();
 }
 
@@ -349,6 +353,7 @@ cudaError_t launch_outer_check(int n, OState* ost, const double* rr, const doubl
 template <int NR>
 __global__ void __launch_bounds__(KB<P64, NR>::MAXT, KB<P64, NR>::MINB) k_norm2(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                 CField<P64> f, SolverCtx ctx) {
+    pdl_enter();
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y * NR;
@@ -372,9 +377,9 @@ __global__ void __launch_bounds__(KB<P64, NR>::MAXT, KB<P64, NR>::MINB) k_norm2(
 
 cudaError_t launch_norm2(const LaunchCfg& c, FieldPtr f, const SolverCtx* ctx, double* out, cudaStream_t st) {
     if (c.NR == 1)
-        k_norm2<1><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(f), *ctx);
+        launch_pdl(k_norm2<1>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs, cf<P64>(f), *ctx);
     else if (c.NR == 2)
-        k_norm2<2><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(f), *ctx);
+        launch_pdl(k_norm2<2>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs, cf<P64>(f), *ctx);
     else
         return cudaErrorInvalidValue;
     launch_finish<1, double, FIN_NORM, double>(c, *ctx, out, 0, st);
@@ -385,6 +390,7 @@ cudaError_t launch_norm2(const LaunchCfg& c, FieldPtr f, const SolverCtx* ctx, d
 // out[l*nrhs + i] = <a_i, b_i> (complex, sum conj(a) b) for every (lattice, rhs)
 __global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_dot64(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                           CField<P64> a, CField<P64> b, SolverCtx ctx) {
+    pdl_enter();
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y;
@@ -406,6 +412,7 @@ __global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_dot64(const LatDev* __rest
 __global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_multi_axpy64(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                                  int nvec, const double2* const* __restrict__ xs,
                                                                  const double2* __restrict__ c, double2* __restrict__ y) {
+    pdl_enter();
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y;
@@ -432,6 +439,7 @@ __global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_multi_axpy64(const LatDev*
 // out = gamma_5 in (spin components 2, 3 negated)
 __global__ void k_gamma5_64(long long n_per_rhs_planes, int Vpad, const double2* __restrict__ in, double2* __restrict__ out,
                             long long total) {
+    pdl_enter();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int comp = (int)((i / Vpad) % 12);
         const double2 v = in[i];
@@ -442,20 +450,20 @@ __global__ void k_gamma5_64(long long n_per_rhs_planes, int Vpad, const double2*
 
 cudaError_t launch_dot64(const LaunchCfg& c, FieldPtr a, FieldPtr b, const SolverCtx* ctx, double2* out,
                          cudaStream_t st) {
-    k_dot64<<<c.nblocks, dim3(c.TS, c.nrhs), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<P64>(a), cf<P64>(b), *ctx);
+    launch_pdl(k_dot64, dim3(c.nblocks), dim3(dim3(c.TS, c.nrhs)), st, c.lats, c.nlat, c.nrhs, cf<P64>(a), cf<P64>(b), *ctx);
     launch_finish<2, double, FIN_DOT, double>(c, *ctx, reinterpret_cast<double*>(out), 0, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_multi_axpy64(const LaunchCfg& c, int nvec, const double2* const* xs, const double2* coef,
                                 FieldPtr y, cudaStream_t st) {
-    k_multi_axpy64<<<c.nblocks, dim3(c.TS, c.nrhs), 0, st>>>(c.lats, c.nlat, c.nrhs, nvec, xs, coef,
+    launch_pdl(k_multi_axpy64, dim3(c.nblocks), dim3(dim3(c.TS, c.nrhs)), st, c.lats, c.nlat, c.nrhs, nvec, xs, coef,
                                                             reinterpret_cast<double2*>(y.v));
     return cudaGetLastError();
 }
 
 cudaError_t launch_gamma5_64(long long total_elems, int Vpad, FieldPtr in, FieldPtr out, cudaStream_t st) {
-    k_gamma5_64<<<4 * 152, 256, 0, st>>>(0, Vpad, reinterpret_cast<const double2*>(in.v),
+    launch_pdl(k_gamma5_64, dim3(4 * 152), dim3(256), st, 0, Vpad, reinterpret_cast<const double2*>(in.v),
                                           reinterpret_cast<double2*>(out.v), total_elems);
     return cudaGetLastError();
 }

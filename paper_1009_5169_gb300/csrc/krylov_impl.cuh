@@ -265,6 +265,7 @@ constexpr int FIN_THREADS = 512;
 template <int NQ, typename A, int MODE, typename RV>
 __global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict__ lats, int nrhs, int nblocks,
                                                          SolverCtx ctx, double* __restrict__ out, int maxiter) {
+    pdl_enter();
     __shared__ double sres[MAX_RHS * 3];
     const int l = blockIdx.x;
     const int blk0 = lats[l].blk0, nblk = lats[l].nblk;
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict
 
 template <int NQ, typename A, int MODE, typename RV>
 inline void launch_finish(const LaunchCfg& c, const SolverCtx& ctx, double* out, int maxiter, cudaStream_t st) {
-    k_finish<NQ, A, MODE, RV><<<c.nlat, FIN_THREADS, 0, st>>>(c.lats, c.nrhs, c.nblocks, ctx, out, maxiter);
+    launch_pdl(k_finish<NQ, A, MODE, RV>, dim3(c.nlat), dim3(FIN_THREADS), st, c.lats, c.nrhs, c.nblocks, ctx, out, maxiter);
 }
 
 template <typename R, typename A>
@@ -392,6 +393,7 @@ template <typename PI, typename PO, int NR, bool DAG>
 __global__ void __launch_bounds__(KB<PI, NR>::MAXT, KB<PI, NR>::MINB) k_hop(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
                                               CField<PI> in, Field<PO> out, double coef, int kpow,
                                               const KState* __restrict__ st) {
+    pdl_enter();
     using R = typename PI::real;
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
@@ -428,6 +430,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_tail(con
                                                CField<PH> hin, CField<PV> xv, CField<PV> zv, Field<PV> out,
                                                CField<PV> ra, double a, double coef, int kpow,
                                                SolverCtx ctx) {
+    pdl_enter();
     using RH = typename PH::real;
     using RV = typename PV::real;
     constexpr int NQ = (RED == RED_TS) ? 3 : (RED == RED_R0V) ? 2 : 1;
@@ -499,6 +502,7 @@ template <typename PV, typename PH, int NR>
 __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_s_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                    CField<PV> r, CField<PV> v, Field<PV> s, Field<PH> sh,
                                                    const KState* __restrict__ st) {
+    pdl_enter();
     using RV = typename PV::real;
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
@@ -532,6 +536,7 @@ template <typename PV, int NR>
 __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_xr_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                     Field<PV> x, Field<PV> r, CField<PV> p, CField<PV> s,
                                                     CField<PV> t, CField<PV> r0f, SolverCtx ctx) {
+    pdl_enter();
     using RV = typename PV::real;
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
@@ -586,6 +591,7 @@ template <typename PV, typename PH, int NR>
 __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_p_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                    Field<PV> p, Field<PH> ph, CField<PV> r, CField<PV> v,
                                                    SolverCtx ctx) {
+    pdl_enter();
     using RV = typename PV::real;
     constexpr bool COPY = !std::is_same<PV, PH>::value;
     const int l = find_lattice(lats, nlat, blockIdx.x);
@@ -630,6 +636,7 @@ template <typename PV, typename PH, int NR>
 __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_inner_init(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                      CField<P64> r64, Field<PV> x, Field<PV> r, Field<PV> r0f,
                                                      Field<PV> p, Field<PH> ph, SolverCtx ctx) {
+    pdl_enter();
     using RV = typename PV::real;
     constexpr bool COPY = !std::is_same<PV, PH>::value;
     const int l = find_lattice(lats, nlat, blockIdx.x);
@@ -679,6 +686,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_inner_in
 template <typename PV, int NR>
 __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_dc_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
                                                     Field<P64> x64, CField<PV> x, SolverCtx ctx) {
+    pdl_enter();
     using RV = typename PV::real;
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
@@ -720,6 +728,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_dc_updat
 // canonical AoS FP64 [rhs][Vh][12 complex] of one lattice <-> field
 template <typename P>
 __global__ void k_pack(const LatDev* __restrict__ lat, int nrhs, const double* __restrict__ aos, Field<P> out) {
+    pdl_enter();
     using R = typename P::real;
     const LatDev g = *lat;
     const int rhs = blockIdx.y;
@@ -737,6 +746,7 @@ __global__ void k_pack(const LatDev* __restrict__ lat, int nrhs, const double* _
 
 template <typename P>
 __global__ void k_unpack(const LatDev* __restrict__ lat, int nrhs, CField<P> in, double* __restrict__ aos) {
+    pdl_enter();
     using R = typename P::real;
     const LatDev g = *lat;
     const int rhs = blockIdx.y;
@@ -770,10 +780,10 @@ struct OpsImpl {
         const KState* ks = ctx ? ctx->st : nullptr;
         SF_NR_SWITCH(c.NR, {
             if (dag)
-                k_hop<PH, PH, NR_, true><<<c.nblocks, block_of(c), 0, st>>>(
+                launch_pdl(k_hop<PH, PH, NR_, true>, dim3(c.nblocks), dim3(block_of(c)), st, 
                     c.lats, c.nlat, c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
             else
-                k_hop<PH, PH, NR_, false><<<c.nblocks, block_of(c), 0, st>>>(
+                launch_pdl(k_hop<PH, PH, NR_, false>, dim3(c.nblocks), dim3(block_of(c)), st, 
                     c.lats, c.nlat, c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
         });
         return cudaGetLastError();
@@ -786,7 +796,7 @@ struct OpsImpl {
         const dim3 b = block_of(c);
         const bool hz = zv.v != nullptr;
 #define SF_TAIL(RED, HZ)                                                                              \
-    k_tail<PH, PV, NR, DAG, RED, HZ><<<c.nblocks, b, 0, st>>>(c.lats, c.nlat, c.nrhs, out_par, cf<PH>(hin), \
+    launch_pdl(k_tail<PH, PV, NR, DAG, RED, HZ>, dim3(c.nblocks), dim3(b), st, c.lats, c.nlat, c.nrhs, out_par, cf<PH>(hin), \
                                                               cf<PV>(xv), cf<PV>(zv), wf<PV>(out), cf<PV>(ra), \
                                                               a, coef, kpow, k)
         using A = typename AccOf<typename PV::real>::T;
@@ -824,7 +834,7 @@ struct OpsImpl {
     static cudaError_t init(const LaunchCfg& c, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
                             FieldPtr ph, const SolverCtx* ctx, int maxiter, cudaStream_t st) {
         SF_NR_SWITCH(c.NR, {
-            k_inner_init<PV, PH, NR_><<<c.nblocks, block_of(c), 0, st>>>(
+            launch_pdl(k_inner_init<PV, PH, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, 
                 c.lats, c.nlat, c.nrhs, cf<P64>(r64), wf<PV>(x), wf<PV>(r), wf<PV>(r0), wf<PV>(p), wf<PH>(ph),
                 *ctx);
         });
@@ -836,7 +846,7 @@ struct OpsImpl {
     static cudaError_t s_update(const LaunchCfg& c, FieldPtr r, FieldPtr v, FieldPtr s, FieldPtr sh,
                                 const SolverCtx* ctx, cudaStream_t st) {
         SF_NR_SWITCH(c.NR, {
-            k_s_update<PV, PH, NR_><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, cf<PV>(r),
+            launch_pdl(k_s_update<PV, PH, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs, cf<PV>(r),
                                                                         cf<PV>(v), wf<PV>(s), wf<PH>(sh), ctx->st);
         });
         return cudaGetLastError();
@@ -845,7 +855,7 @@ struct OpsImpl {
     static cudaError_t xr_update(const LaunchCfg& c, FieldPtr x, FieldPtr r, FieldPtr p, FieldPtr s, FieldPtr t,
                                  FieldPtr r0, const SolverCtx* ctx, cudaStream_t st) {
         SF_NR_SWITCH(c.NR, {
-            k_xr_update<PV, NR_><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, wf<PV>(x), wf<PV>(r),
+            launch_pdl(k_xr_update<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs, wf<PV>(x), wf<PV>(r),
                                                                      cf<PV>(p), cf<PV>(s), cf<PV>(t), cf<PV>(r0),
                                                                      *ctx);
         });
@@ -856,7 +866,7 @@ struct OpsImpl {
     static cudaError_t p_update(const LaunchCfg& c, FieldPtr p, FieldPtr ph, FieldPtr r, FieldPtr v,
                                 const SolverCtx* ctx, cudaStream_t st) {
         SF_NR_SWITCH(c.NR, {
-            k_p_update<PV, PH, NR_><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, wf<PV>(p),
+            launch_pdl(k_p_update<PV, PH, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs, wf<PV>(p),
                                                                         wf<PH>(ph), cf<PV>(r), cf<PV>(v), *ctx);
         });
         return cudaGetLastError();
@@ -865,7 +875,7 @@ struct OpsImpl {
     static cudaError_t dc_update(const LaunchCfg& c, FieldPtr x64, FieldPtr x, const SolverCtx* ctx,
                                  cudaStream_t st) {
         SF_NR_SWITCH(c.NR, {
-            k_dc_update<PV, NR_><<<c.nblocks, block_of(c), 0, st>>>(c.lats, c.nlat, c.nrhs, wf<P64>(x64),
+            launch_pdl(k_dc_update<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs, wf<P64>(x64),
                                                                      cf<PV>(x), *ctx);
         });
         return cudaGetLastError();

@@ -22,6 +22,17 @@
 
 namespace sf {
 
+// ------------------------------------------------- programmatic launches
+// The solver's kernels are launched with programmatic stream serialization:
+// the next kernel of the stream may be scheduled while this one drains.
+// Every such kernel first waits for its predecessor to complete and flush
+// (griddepcontrol.wait; a no-op for a plain launch), then lets its own
+// successor start launching.  The wait is the hardware's, no spin of ours.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // ------------------------------------------------------------- complex
 template <typename R>
 struct cpx {

@@ -94,6 +94,23 @@ struct KrylovOps {
     cudaError_t (*unpack_h)(const LaunchCfg&, FieldPtr in, double* aos, cudaStream_t);
 };
 
+// Launch a kernel of this library with programmatic stream serialization
+// (it starts with pdl_enter(), see sf_device.cuh).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 const KrylovOps& ops_f64();
 const KrylovOps& ops_f32();
 const KrylovOps& ops_f32h16();
