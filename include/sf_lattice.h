@@ -154,7 +154,7 @@ void sf_lattice_destroy(sf_lattice* lat);
 sf_status wilson_apply_block(sf_lattice* lat, sf_op op, sf_prec prec, int nrhs, const double* in,
                              double* out);
 
-/* Alg. 2, lines 2-3, on the even sites: X = Dhat^{-1} Phi and, if Y is not
+/* The two solves of Alg. 2 on the even sites: X = Dhat^{-1} Phi and, if Y is not
  * NULL, Y = Dhat^{-dag} X, each to |b - A x| <= tol |b| per right-hand side,
  * checked on an FP64 recomputation of the residual.  All nrhs systems run
  * as one block (one launch per kernel for all of them).  maxiter bounds the
@@ -163,7 +163,7 @@ sf_status wilson_apply_block(sf_lattice* lat, sf_op op, sf_prec prec, int nrhs, 
 sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* X, double* Y,
                       double tol, int maxiter, sf_solve_info* info);
 
-/* Eq. (3) with Alg. 2, lines 4-6: the force of S = sum_i |Dhat^{-1} phi_i|^2
+/* Eq. (3) with the force steps of Alg. 2: the force of S = sum_i |Dhat^{-1} phi_i|^2
  * from x_i = Dhat^{-1} phi_i and y_i = Dhat^{-dag} x_i (even sites).  Writes
  * F (force layout, may be NULL) and, if mom is not NULL, does mom -= eps F
  * in FP64 (mom in the force layout). */

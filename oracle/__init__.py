@@ -153,7 +153,7 @@ def bicgstab(U, b_e, L, T, theta, kappa, tol=1e-12, maxiter=10000, dagger=False)
 
 
 def force(U, X_e, Y_e, L, T, theta, kappa):
-    """MD force F_mu(n) = sum_i f[x_i, y_i] of Eq. (3) (Alg. 2, lines 4-6),
+    """MD force F_mu(n) = sum_i f[x_i, y_i] of Eq. (3) (the force steps of Alg. 2),
     the gradient of S = sum_i |Dhat^-1 phi_i|^2 with respect to
     U_mu(x) -> exp(i omega^a T^a) U_mu(x).  Shape [(T+1)L^3, 4, 8]."""
     X_e = _block(X_e, L, T, True)
@@ -203,7 +203,7 @@ def gamma5(psi):
 
 
 def solve_pair(U, phi_e, L, T, theta, kappa, tol=1e-12, maxiter=10000):
-    """Alg. 2 lines 2-3 by the sequential solver: X = Dhat^-1 Phi,
+    """The two solves of Alg. 2 by the sequential solver: X = Dhat^-1 Phi,
     Y = Dhat^-dag X.  Returns (X, Y, info dict)."""
     X, itx, rx = bicgstab(U, phi_e, L, T, theta, kappa, tol, maxiter, dagger=False)
     Y, ity, ry = bicgstab(U, X, L, T, theta, kappa, tol, maxiter, dagger=True)

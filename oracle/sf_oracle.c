@@ -486,7 +486,7 @@ int sfo_bicgstab(int L, int T, double theta, double kappa, const double* U, int 
 
 /*
  * MD force of Eq. (3) for S = sum_i |Dhat^-1 phi_i|^2 given x_i = Dhat^-1 phi_i
- * and y_i = Dhat^-dag x_i on the even sites (Alg. 2, lines 2-3).
+ * and y_i = Dhat^-dag x_i on the even sites (the two solves of Alg. 2).
  *
  * With Xh = (x_e, kappa H_oe x_e) and Yh = (y_e, kappa gamma_5 H_oe gamma_5 y_e)
  * on the full lattice, dS = 2 kappa Re sum_i Yh_i^dag dH Xh_i, so for the

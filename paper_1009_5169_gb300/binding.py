@@ -219,7 +219,7 @@ def wilson_hop_resident(lat: Lattice, prec: str, nrhs: int, out_parity: int = 1)
 
 def solve_block(lat: Lattice, algo: str, phi, X, Y=None, tol: float = 1e-10, maxiter: int = 10000,
                 allow_noconv: bool = False) -> dict:
-    """Alg. 2 lines 2-3: X = Dhat^-1 phi, Y = Dhat^-dag X.  Returns the info dict."""
+    """The two solves of Alg. 2: X = Dhat^-1 phi, Y = Dhat^-dag X.  Returns the info dict."""
     nrhs = _nrhs_of(phi, lat.Vh * 24 * 8)
     _check_size(X, nrhs * lat.Vh * 24 * 8, "X")
     if Y is not None:

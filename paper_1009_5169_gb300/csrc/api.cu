@@ -3,7 +3,7 @@
 // autotuner, the graph-captured BiCGStab loop and the FP64 defect-correction
 // driver around it.
 //
-// Solve structure (Alg. 2, lines 2-3; mixed precision as in Sec. 3.2):
+// Solve structure (the two solves of Alg. 2; mixed precision as in Sec. 3.2):
 //   x = 0; repeat { r = phi - Dhat x (FP64);  stop if |r| <= tol |phi|;
 //                   solve Dhat e = r/|r| with BiCGStab in the inner precision
 //                   to max(delta_prec, 0.1 tol |phi|/|r|);  x += |r| e }

@@ -1,6 +1,6 @@
 // gauge.cu -- gauge-field kernels: link preparation into the hop layouts,
 // the SU(3) check of an input field, the SF plaquette action (Sec. 4) and the
-// MD force of Eq. (3) summed over the pseudo-fermion fields (Alg. 2, lines 4-6).
+// MD force of Eq. (3) summed over the pseudo-fermion fields (the force steps of Alg. 2).
 #include <type_traits>
 
 #include "krylov_impl.cuh"
