@@ -60,13 +60,13 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(key, TS, NR):
+def _ncu_traffic(key, TS, NR, pipe=0):
     """Per-launch DRAM bytes of the dslash kernel at this tiling from the
     committed ncu summary, if it was taken on the current kernel source."""
     try:
         with open(os.path.join(ROOT, "profiles", "dslash_traffic.json")) as f:
             d = json.load(f)
-        e = d.get(f"{key}:TS{TS}NR{NR}")
+        e = d.get(f"{key}:TS{TS}NR{NR}" + (":pipe" if pipe else ""))
         if e and e.get("kernel_hash") == _kernel_hash():
             return e
     except Exception:
@@ -227,7 +227,7 @@ def run_ours(args, rank, world, local_rank):
     # ---------------- roofline of the dominant kernel: the FP32 dslash (hop)
     peak, peak_kind = _peaks()
     prec = "fp32" if args.algo == "mixed_dc" else ("fp16" if args.algo == "mixed_dc_half" else "fp64")
-    TS, NR = lat.get_tuning(prec, nrhs)
+    TS, NR, PIPE = lat.get_tuning(prec, nrhs)
     Vh = lt.Vh
     site_bytes = {"fp32": nrhs * 96 * 2 + 8 * 48, "fp16": nrhs * 52 * 2 + 8 * 24,
                   "fp64": nrhs * 192 * 2 + 8 * 144}[prec]
@@ -252,10 +252,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_warm = a.elapsed_time(b) * 1e-3 / reps
     achieved = alg_bytes / t_cold / 1e9
-    tr = _ncu_traffic(f"{args.workload}:{prec}", TS, NR)
+    tr = _ncu_traffic(f"{args.workload}:{prec}", TS, NR, PIPE)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                "kernel": f"k_hop<{prec}> (dslash H_oe), TS={TS}, NR={NR}, L2 flushed before each launch",
+                "kernel": f"k_hop<{prec}> (dslash H_oe), TS={TS}, NR={NR}, pipelined={PIPE}, "
+                          "L2 flushed before each launch",
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_us": round(t_cold * 1e6, 2),
                 "l2_warm_launch_us": round(t_warm * 1e6, 2), "peak_kind": peak_kind}
 
@@ -268,7 +269,7 @@ def run_ours(args, rank, world, local_rank):
         del Ub
         res = {}
         for p in ("fp32", "fp16"):
-            TSb, NRb = big.get_tuning(p, nrhs)
+            TSb, NRb, PIPEb = big.get_tuning(p, nrhs)
             sf.wilson_hop_resident(big, p, nrhs, 1)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -291,11 +292,12 @@ def run_ours(args, rank, world, local_rank):
             Vhb = Lh ** 3 * (Th - 1) // 2
             sb = {"fp32": nrhs * 96 * 2 + 8 * 48, "fp16": nrhs * 52 * 2 + 8 * 24}[p]
             ab = Vhb * sb
-            trb = _ncu_traffic(f"sf24:{p}", TSb, NRb)
+            trb = _ncu_traffic(f"sf24:{p}", TSb, NRb, PIPEb)
             res[p] = {"achieved": round(ab / t / 1e9, 1), "frac": round(ab / t / 1e9 / peak, 4),
                       "launch_us": round(t * 1e6, 2), "achieved_l2_flushed": round(ab / tc / 1e9, 1),
                       "launch_us_l2_flushed": round(tc * 1e6, 2), "algorithmic_bytes_per_launch": ab,
-                      "TS": TSb, "NR": NRb, "traffic": trb["dram_bytes_per_launch"] if trb else None}
+                      "TS": TSb, "NR": NRb, "pipelined": PIPEb,
+                      "traffic": trb["dram_bytes_per_launch"] if trb else None}
         big.close()
         hbm = {"lattice": f"{Lh}^3x{Th} SF, 5 RHS (working set per launch larger than L2)", "unit": "GB/s",
                "peak": peak, **res}
@@ -382,7 +384,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": f"{args.workload}: {lt.L}^3x{lt.T} SF, eps {lt.eps}, kappa {lt.kappa}, "
                                f"theta {lt.theta}, {nrhs} RHS, tol {tol}, X and Y solves + force",
                    "algo": args.algo, "l2": "flushed between steps", "parallelism": f"replicas x{world}",
-                   "tiling": {"fp64": lat.get_tuning("fp64", nrhs), prec: (TS, NR)}},
+                   "tiling": {"fp64": lat.get_tuning("fp64", nrhs), prec: (TS, NR, PIPE)}},
         "accuracy": {"max_true_rel_resid": resid, "sweeps_x": last["iters_outer"], "inner_iters_x": last["iters_inner"],
                      "sweeps_y": last["iters_outer_y"], "inner_iters_y": last["iters_inner_y"]},
         "roofline": roofline, "dslash_hbm": hbm, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -564,8 +566,8 @@ def run_dslash_only(args, local_rank):
     res = {}
     Vh = L ** 3 * (T - 1) // 2
     for p in args.dslash_precs.split(","):
-        TS, NR = args.tiling
-        lat.set_tuning(p, TS, NR)
+        TS, NR, PIPE = (list(args.tiling) + [0])[:3]
+        lat.set_tuning(p, TS, NR, PIPE if p != "fp64" else 0)
         sf.wilson_hop_resident(lat, p, 5, 1)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -603,7 +605,8 @@ def main():
     ap.add_argument("--dslash-only", action="store_true", help="time the hop kernel alone (profiling aid)")
     ap.add_argument("--dslash-lattice", type=int, nargs=2, default=(32, 24), metavar=("L", "T"))
     ap.add_argument("--dslash-precs", default="fp32,fp16")
-    ap.add_argument("--tiling", type=int, nargs=2, default=(64, 1), metavar=("TS", "NR"))
+    ap.add_argument("--tiling", type=int, nargs="+", default=(64, 1), metavar="N",
+                    help="TS NR [pipe]: sites per tile, rhs per thread, pipelined hop (0/1)")
     ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)

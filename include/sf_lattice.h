@@ -139,12 +139,15 @@ sf_status sf_lattice_set_links(sf_lattice* lat, const double* links);
  * (1, 2, 3 or 5; FP64: 1 or 2).  A block holds TS * ceil(nrhs / NR) threads,
  * at most 256 (FP64, NR = 1), 128 (FP64, NR = 2), 320 / 384 / 256 (FP32 and
  * FP16 with NR = 1 / 2 / 3 or 5): checked when a solve or apply uses the
- * tiling, SF_EINVAL beyond.  TS = 0 restores autotuning. */
-sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR);
+ * tiling, SF_EINVAL beyond.  pipe = 1 selects the pipelined hop (operands of
+ * the next hops loaded while the current one is applied; FP32 / FP16 only,
+ * NR = 1 or 2, at most 256 threads), pipe = 0 the plain one.  TS = 0
+ * restores autotuning (TS, NR and pipe). */
+sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR, int pipe);
 
 /* Tiling in use for a precision and block size (runs the autotuner if it has
- * not run yet). */
-sf_status sf_lattice_get_tuning(sf_lattice* lat, sf_prec prec, int nrhs, int* TS, int* NR);
+ * not run yet); pipe may be NULL. */
+sf_status sf_lattice_get_tuning(sf_lattice* lat, sf_prec prec, int nrhs, int* TS, int* NR, int* pipe);
 
 void sf_lattice_destroy(sf_lattice* lat);
 

@@ -67,8 +67,8 @@ def lib() -> ctypes.CDLL:
         vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         L.sf_lattice_create.argtypes = [ctypes.POINTER(vp), i, i, d, d, d, vp, i, vp]
         L.sf_lattice_set_links.argtypes = [vp, vp]
-        L.sf_lattice_set_tuning.argtypes = [vp, i, i, i]
-        L.sf_lattice_get_tuning.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.sf_lattice_set_tuning.argtypes = [vp, i, i, i, i]
+        L.sf_lattice_get_tuning.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
         L.sf_lattice_destroy.argtypes = [vp]
         L.sf_lattice_destroy.restype = None
         L.wilson_apply_block.argtypes = [vp, i, i, i, vp, vp]
@@ -165,13 +165,16 @@ class Lattice:
         _check_size(links, (self.T + 1) * self.L ** 3 * 4 * 18 * 8, "links")
         _check(lib().sf_lattice_set_links(self._h, _ptr(links)))
 
-    def set_tuning(self, prec: str, TS: int, NR: int) -> None:
-        _check(lib().sf_lattice_set_tuning(self._h, PRECS[prec], TS, NR))
+    def set_tuning(self, prec: str, TS: int, NR: int, pipe: int = 0) -> None:
+        """Fix (TS sites per tile, NR rhs per thread, pipelined hop 0/1); TS = 0 autotunes."""
+        _check(lib().sf_lattice_set_tuning(self._h, PRECS[prec], TS, NR, pipe))
 
     def get_tuning(self, prec: str, nrhs: int):
-        ts, nr = ctypes.c_int(), ctypes.c_int()
-        _check(lib().sf_lattice_get_tuning(self._h, PRECS[prec], nrhs, ctypes.byref(ts), ctypes.byref(nr)))
-        return ts.value, nr.value
+        """(TS, NR, pipe) in use for nrhs right-hand sides (autotunes on first use)."""
+        ts, nr, pp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().sf_lattice_get_tuning(self._h, PRECS[prec], nrhs, ctypes.byref(ts), ctypes.byref(nr),
+                                           ctypes.byref(pp)))
+        return ts.value, nr.value, pp.value
 
     def close(self) -> None:
         if self._h:

@@ -13,6 +13,7 @@
 // convergence flags, so an inner solve costs one graph launch and the host
 // synchronises once per outer sweep.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -164,7 +165,7 @@ struct sf_lattice {
     DevMem canon, u64, u32, u16;
     DevMem scratch;      // plaquette partials + scalars
     DevMem stage_in, stage_out;  // device staging for host arrays
-    int tune_TS[3] = {0, 0, 0}, tune_NR[3] = {0, 0, 0};
+    int tune_TS[3] = {0, 0, 0}, tune_NR[3] = {0, 0, 0}, tune_pipe[3] = {0, 0, 0};
     struct Workspace* ws = nullptr;  // own solver workspace (created on first use)
     sf_cnn* cnn = nullptr;           // learned preconditioner for SF_SOLVE_FGCR_CNN (not owned)
 
@@ -200,12 +201,14 @@ struct sf_lattice {
 // operands, 3 FP64 vector kernels) are compiled for: blocks of TS sites x
 // ceil(nrhs / NR) right-hand-side groups within the kernels' launch bounds
 // (FP64: NR = 1 or 2; FP32 / FP16: NR = 1, 2, 3 or 5).
-inline bool tiling_ok(int ci, int TS, int NR, int nrhs) {
+inline bool tiling_ok(int ci, int TS, int NR, int nrhs, int pipe = 0) {
     const int threads = TS * ((nrhs + NR - 1) / NR);
     if (ci == 1 || ci == 2) {
         if (NR != 1 && NR != 2 && NR != 3 && NR != 5) return false;
+        if (pipe) return NR <= 2 && threads <= 256;
         return threads <= (NR == 1 ? 320 : NR == 2 ? 384 : 256);
     }
+    if (pipe) return false;
     if (NR != 1 && NR != 2) return false;
     return threads <= (NR == 1 ? 256 : 128);
 }
@@ -229,7 +232,7 @@ struct Workspace {
     std::vector<long long> soff;
 
     struct Cfg {
-        int TS = 0, NR = 0, nblocks = 0;
+        int TS = 0, NR = 0, nblocks = 0, pipe = 0;
         bool ready = false;
         DevMem lats_dev;
         std::vector<LatDev> host;
@@ -295,10 +298,11 @@ struct Workspace {
         CK(cudaHostAlloc(&pin, 8 * sizeof(int), cudaHostAllocDefault));
     }
 
-    void set_tiling(int ci, int TS, int NR) {
+    void set_tiling(int ci, int TS, int NR, int pipe = 0) {
         Cfg& c = cfg[ci];
         c.TS = TS;
         c.NR = NR;
+        c.pipe = pipe;
         c.host.resize(nlat);
         int blk = 0;
         for (int l = 0; l < nlat; ++l) {
@@ -313,11 +317,11 @@ struct Workspace {
         c.nblocks = blk;
         c.lats_dev.ensure(sizeof(LatDev) * nlat);
         CK(cudaMemcpy(c.lats_dev.p, c.host.data(), sizeof(LatDev) * nlat, cudaMemcpyHostToDevice));
-        c.lc = LaunchCfg{c.lats_dev.as<LatDev>(), nlat, nrhs, TS, NR, blk};
+        c.lc = LaunchCfg{c.lats_dev.as<LatDev>(), nlat, nrhs, TS, NR, blk, pipe};
         c.per_lat.resize(nlat);
         for (int l = 0; l < nlat; ++l) {
             c.per_lat[l] = LaunchCfg{c.lats_dev.as<LatDev>() + l, 1, nrhs, TS, NR,
-                                     std::max(1, (c.host[l].Vh + 127) / 128)};
+                                     std::max(1, (c.host[l].Vh + 127) / 128), 0};
         }
         c.ready = true;
         // graphs bake launch shapes in
@@ -361,19 +365,10 @@ struct Workspace {
 
     // one BiCGStab iteration on all rhs: 7 kernels and the lattice sums of its 3 reductions
     void enqueue_iteration(int ci, bool dag, const SolverCtx& k, cudaStream_t s) {
-        const KrylovOps& o = ops_for(ci);
-        const LaunchCfg& lc = cfg[ci].lc;
         Inner& in = inner[ci];
-        const FieldPtr none{nullptr, nullptr};
-        CK(o.hop(lc, 1, dag, hop_in(ci, in.p, in.ph), in.tmp.ptr(), 1.0, 0, &k, s));
-        CK(o.tail(lc, 0, dag, RED_R0V, in.tmp.ptr(), in.p.ptr(), none, in.v.ptr(), in.r0.ptr(), 1.0, -1.0, 2, &k,
-                  nullptr, s));
-        CK(o.s_update(lc, in.r.ptr(), in.v.ptr(), in.s.ptr(), in.sh.ptr(), &k, s));
-        CK(o.hop(lc, 1, dag, hop_in(ci, in.s, in.sh), in.tmp.ptr(), 1.0, 0, &k, s));
-        CK(o.tail(lc, 0, dag, RED_TS, in.tmp.ptr(), in.s.ptr(), none, in.t.ptr(), none, 1.0, -1.0, 2, &k, nullptr,
-                  s));
-        CK(o.xr_update(lc, in.x.ptr(), in.r.ptr(), in.p.ptr(), in.s.ptr(), in.t.ptr(), in.r0.ptr(), &k, s));
-        CK(o.p_update(lc, in.p.ptr(), in.ph.ptr(), in.r.ptr(), in.v.ptr(), &k, s));
+        const IterFields f{in.x.ptr(), in.r.ptr(), in.r0.ptr(), in.p.ptr(), in.v.ptr(),
+                           in.s.ptr(), in.t.ptr(), in.tmp.ptr(), in.ph.ptr(), in.sh.ptr()};
+        CK(ops_for(ci).iterate(cfg[ci].lc, dag, f, &k, s));
     }
 
     GraphEntry& graph(int ci, bool dag) {
@@ -422,10 +417,11 @@ struct Workspace {
         }
         // explicit tiling of the (single) lattice wins
         if (nlat == 1 && lats[0]->tune_TS[ci] > 0) {
-            const int TS = lats[0]->tune_TS[ci], NR = lats[0]->tune_NR[ci];
-            REQUIRE(tiling_ok(ci, TS, NR, nrhs),
-                    "tiling exceeds the block size of this precision (TS * ceil(nrhs / NR) threads)");
-            set_tiling(ci, TS, NR);
+            const int TS = lats[0]->tune_TS[ci], NR = lats[0]->tune_NR[ci], pipe = lats[0]->tune_pipe[ci];
+            REQUIRE(tiling_ok(ci, TS, NR, nrhs, pipe),
+                    "tiling exceeds the block size of this precision (TS * ceil(nrhs / NR) threads; "
+                    "pipelined hop: FP32 / FP16, NR <= 2, at most 256 threads)");
+            set_tiling(ci, TS, NR, pipe);
             return;
         }
         autotune(ci);
@@ -538,7 +534,7 @@ struct Workspace {
             CK(cudaMemcpyAsync(pin + 1, loop_count.p, sizeof(int), cudaMemcpyDeviceToHost, s));
             launches += 3;  // init (+ its sums), dc_update
             CK(cudaStreamSynchronize(s));
-            launches += 10LL * pin[1];  // kernels of one iteration
+            launches += (long long)o.iteration_kernels(cfg[ci].lc) * pin[1];
         }
         std::vector<OState> out(n);
         CK(cudaMemcpy(out.data(), ost.p, n * sizeof(OState), cudaMemcpyDeviceToHost));
@@ -566,7 +562,7 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::map<TuneKey, std::array<int, 3>> g_tune_cache;  // TS, NR, pipe
 
 }  // namespace
 
@@ -580,7 +576,7 @@ void Workspace::autotune(int ci) {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            set_tiling(ci, it->second.first, it->second.second);
+            set_tiling(ci, it->second[0], it->second[1], it->second[2]);
             return;
         }
     }
@@ -592,41 +588,43 @@ void Workspace::autotune(int ci) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bTS = 64, bNR = 1;
+    int bTS = 64, bNR = 1, bpipe = 0;
     const FieldPtr none{nullptr, nullptr};
-    for (int NR : nrs_all) {
-        if (NR > nrhs) continue;
-        for (int TS : tss) {
-            if (!tiling_ok(ci, TS, NR, nrhs)) continue;
-            set_tiling(ci, TS, NR);
-            const LaunchCfg& lc = cfg[ci].lc;
-            Inner& in = inner[ci];
-            auto run = [&]() {
-                CK(o.hop(lc, 1, false, hop_in(ci, in.p, in.ph), in.tmp.ptr(), 1.0, 0, nullptr, stream));
-                CK(o.tail(lc, 0, false, RED_NONE, in.tmp.ptr(), in.p.ptr(), none, in.v.ptr(), none, 1.0, -1.0, 2,
-                          nullptr, nullptr, stream));
-            };
-            run();
-            run();
-            CK(cudaEventRecord(e0, stream));
-            const int reps = 5;
-            for (int r = 0; r < reps; ++r) run();
-            CK(cudaEventRecord(e1, stream));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
-                bTS = TS;
-                bNR = NR;
+    for (int pipe = 0; pipe <= 1; ++pipe)
+        for (int NR : nrs_all) {
+            if (NR > nrhs) continue;
+            for (int TS : tss) {
+                if (!tiling_ok(ci, TS, NR, nrhs, pipe)) continue;
+                set_tiling(ci, TS, NR, pipe);
+                const LaunchCfg& lc = cfg[ci].lc;
+                Inner& in = inner[ci];
+                auto run = [&]() {
+                    CK(o.hop(lc, 1, false, hop_in(ci, in.p, in.ph), in.tmp.ptr(), 1.0, 0, nullptr, stream));
+                    CK(o.tail(lc, 0, false, RED_NONE, in.tmp.ptr(), in.p.ptr(), none, in.v.ptr(), none, 1.0, -1.0,
+                              2, nullptr, nullptr, stream));
+                };
+                run();
+                run();
+                CK(cudaEventRecord(e0, stream));
+                const int reps = 12;
+                for (int r = 0; r < reps; ++r) run();
+                CK(cudaEventRecord(e1, stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    bTS = TS;
+                    bNR = NR;
+                    bpipe = pipe;
+                }
             }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    set_tiling(ci, bTS, bNR);
+    set_tiling(ci, bTS, bNR, bpipe);
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tune_cache[key] = {bTS, bNR};
+    g_tune_cache[key] = {bTS, bNR, bpipe};
 }
 
 
@@ -918,7 +916,7 @@ sf_status sf_lattice_set_links(sf_lattice* lat, const double* links) {
     });
 }
 
-sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR) {
+sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR, int pipe) {
     return guarded([&] {
         REQUIRE(lat != nullptr, "lattice is NULL");
         REQUIRE(prec >= SF_FP64 && prec <= SF_FP16, "bad precision");
@@ -927,14 +925,17 @@ sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR) {
             REQUIRE(TS == 32 || TS == 64 || TS == 128, "TS must be 32, 64 or 128");
             REQUIRE(NR == 1 || NR == 2 || NR == 3 || NR == 5, "NR must be 1, 2, 3 or 5");
             REQUIRE(!(ci == 0 && NR > 2), "FP64 supports NR = 1 or 2");
+            REQUIRE(pipe == 0 || pipe == 1, "pipe must be 0 or 1");
+            REQUIRE(!pipe || (ci != 0 && NR <= 2), "the pipelined hop takes FP32 / FP16 operands and NR = 1 or 2");
         }
         lat->tune_TS[ci] = TS;
         lat->tune_NR[ci] = NR;
+        lat->tune_pipe[ci] = TS != 0 ? pipe : 0;
         if (lat->ws) lat->ws->cfg[ci].ready = false;
     });
 }
 
-sf_status sf_lattice_get_tuning(sf_lattice* lat, sf_prec prec, int nrhs, int* TS, int* NR) {
+sf_status sf_lattice_get_tuning(sf_lattice* lat, sf_prec prec, int nrhs, int* TS, int* NR, int* pipe) {
     return guarded([&] {
         REQUIRE(lat != nullptr && TS != nullptr && NR != nullptr, "NULL argument");
         REQUIRE(prec >= SF_FP64 && prec <= SF_FP16, "bad precision");
@@ -945,6 +946,7 @@ sf_status sf_lattice_get_tuning(sf_lattice* lat, sf_prec prec, int nrhs, int* TS
         w.ensure_cfg(ci);
         *TS = w.cfg[ci].TS;
         *NR = w.cfg[ci].NR;
+        if (pipe) *pipe = w.cfg[ci].pipe;
     });
 }
 

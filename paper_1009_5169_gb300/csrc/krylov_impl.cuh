@@ -56,6 +56,13 @@ struct KB {
     static constexpr int MAXT = F64 ? (NR == 1 ? 256 : 128) : (NR == 1 ? 320 : NR == 2 ? 384 : 256);
     static constexpr int MINB = F64 ? 1 : (NR == 1 ? 2 : 1);
 };
+// hop and tail kernels: the pipelined hop's blocks hold at most 256 threads
+// (up to 255 registers each for the operand buffers)
+template <typename P, int NR, bool PIPE>
+struct KBH {
+    static constexpr int MAXT = PIPE ? 256 : KB<P, NR>::MAXT;
+    static constexpr int MINB = PIPE ? 1 : KB<P, NR>::MINB;
+};
 
 // ------------------------------------------------------------ hop
 template <int MU, typename P, int NR, bool DAG>
@@ -113,6 +120,156 @@ __device__ __forceinline__ void hop_site(const LatDev& g, const SiteX& s, int cb
     hop_dir<1, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
     hop_dir<2, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
     hop_dir<3, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+}
+
+// ------------------------------------------------------------ pipelined hop
+// FP32 / FP16 operands with NR <= 2: the raw operands of hop H (H = 2 mu,
+// + 1 for the backward hop) are loaded PF hops ahead of their use, so a
+// site's eight dependent load round trips overlap about PF at a time.  This
+// pays in registers (PF buffers) what it saves in latency: for small
+// lattices, whose launches hold a few warps per SM; the autotuner chooses.
+template <typename P, int NR> struct HopBuf;
+template <int NR> struct HopBuf<P32, NR> {
+    float4 u[3];       // link rows 0, 1
+    float4 s[NR][6];   // neighbour spinors
+};
+template <int NR> struct HopBuf<P16, NR> {
+    uint2 u[3];
+    uint4 s[NR][3];
+    float sc[NR];
+};
+template <int NR> struct PipeDepth { static constexpr int PF = (NR == 1) ? 4 : 2; };
+
+template <int H, typename P, int NR>
+__device__ __forceinline__ void hop_fetch(const LatDev& g, const SiteX& s, int cb, int out_par, const CField<P>& in,
+                                          int r0, int nval, HopBuf<P, NR>& b, bool& valid) {
+    constexpr int MU = H >> 1;
+    constexpr bool FWD = (H & 1) == 0;
+    valid = (MU != 0) || (FWD ? (s.x0 < g.T - 1) : (s.x0 > 1));
+    if (!valid) return;
+    const int ncb = neighbour_cb<MU, FWD ? +1 : -1>(g, s);
+    const int lpar = FWD ? out_par : (out_par ^ 1);
+    const int lcb = FWD ? cb : ncb;
+    if constexpr (std::is_same<P, P32>::value) {
+        const float4* ub = g.u32 + ((long long)(MU * 2 + lpar) * 3) * g.Vpad + lcb;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b.u[k] = __ldg(ub + (long long)k * g.Vpad);
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if (j < nval) {
+                const float4* sp = in.v + vbase<P32>(g, r0 + j) + ncb;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) b.s[j][k] = __ldg(sp + (long long)k * g.Vpad);
+            }
+    } else {
+        const uint2* ub = g.u16 + ((long long)(MU * 2 + lpar) * 3) * g.Vpad + lcb;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b.u[k] = __ldg(ub + (long long)k * g.Vpad);
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if (j < nval) {
+                const uint4* sp = in.v + vbase<P16>(g, r0 + j) + ncb;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) b.s[j][k] = __ldg(sp + (long long)k * g.Vpad);
+                b.sc[j] = __ldg(in.scale + sbase(g, r0 + j) + ncb);
+            }
+    }
+}
+
+template <int H, typename P, int NR, bool DAG>
+__device__ __forceinline__ void hop_apply(const LatDev& g, const HopBuf<P, NR>& b, bool valid, int nval,
+                                          cpx<float> (&acc)[NR][4][3]) {
+    constexpr int MU = H >> 1;
+    constexpr bool FWD = (H & 1) == 0;
+    constexpr int S = (FWD == DAG) ? +1 : -1;  // projector 1 + S gamma_mu
+    if (!valid) return;
+    Link<float> U;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float2 a, c;
+        if constexpr (std::is_same<P, P32>::value) {
+            a = make_float2(b.u[k].x, b.u[k].y);
+            c = make_float2(b.u[k].z, b.u[k].w);
+        } else {
+            a = h2f(b.u[k].x);
+            c = h2f(b.u[k].y);
+        }
+        U.m[(2 * k) / 3][(2 * k) % 3] = cpx<float>{a.x, a.y};
+        U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = cpx<float>{c.x, c.y};
+    }
+    rebuild_row2<MU>(g, U);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        if (j < nval) {
+            cpx<float> p[4][3];
+            if constexpr (std::is_same<P, P32>::value) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    p[(2 * k) / 3][(2 * k) % 3] = cpx<float>{b.s[j][k].x, b.s[j][k].y};
+                    p[(2 * k + 1) / 3][(2 * k + 1) % 3] = cpx<float>{b.s[j][k].z, b.s[j][k].w};
+                }
+            } else {
+                const float sc = b.sc[j];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float2 a = h2f(b.s[j][k].x), c = h2f(b.s[j][k].y), d = h2f(b.s[j][k].z),
+                                 e = h2f(b.s[j][k].w);
+                    p[(4 * k) / 3][(4 * k) % 3] = cpx<float>{a.x * sc, a.y * sc};
+                    p[(4 * k + 1) / 3][(4 * k + 1) % 3] = cpx<float>{c.x * sc, c.y * sc};
+                    p[(4 * k + 2) / 3][(4 * k + 2) % 3] = cpx<float>{d.x * sc, d.y * sc};
+                    p[(4 * k + 3) / 3][(4 * k + 3) % 3] = cpx<float>{e.x * sc, e.y * sc};
+                }
+            }
+            cpx<float> h[2][3], w[2][3];
+            project<MU, S>(p, h);
+            if (FWD) mul_link(U, h, w);
+            else mul_link_dag(U, h, w);
+            expand_add<MU, S>(acc[j], w);
+        }
+    }
+}
+
+// apply hop H from its buffer, then reuse the buffer for hop H + PF
+template <int H, typename P, int NR, bool DAG, int PF>
+__device__ __forceinline__ void hop_step(const LatDev& g, const SiteX& s, int cb, int out_par, const CField<P>& in,
+                                         int r0, int nval, HopBuf<P, NR> (&b)[PF], bool (&v)[8],
+                                         cpx<float> (&acc)[NR][4][3]) {
+    hop_apply<H, P, NR, DAG>(g, b[H % PF], v[H], nval, acc);
+    if constexpr (H + PF < 8) hop_fetch<H + PF, P, NR>(g, s, cb, out_par, in, r0, nval, b[H % PF], v[H + PF]);
+}
+
+template <typename P, int NR, bool DAG>
+__device__ __forceinline__ void hop_site_pipe(const LatDev& g, const SiteX& s, int cb, int out_par,
+                                              const CField<P>& in, int r0, int nval, cpx<float> (&acc)[NR][4][3]) {
+    constexpr int PF = PipeDepth<NR>::PF;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[j][sp][a] = cpx<float>{0.f, 0.f};
+    HopBuf<P, NR> b[PF];
+    bool v[8];
+    hop_fetch<0, P, NR>(g, s, cb, out_par, in, r0, nval, b[0], v[0]);
+    hop_fetch<1, P, NR>(g, s, cb, out_par, in, r0, nval, b[1 % PF], v[1]);
+    if constexpr (PF > 2) hop_fetch<2, P, NR>(g, s, cb, out_par, in, r0, nval, b[2 % PF], v[2]);
+    if constexpr (PF > 3) hop_fetch<3, P, NR>(g, s, cb, out_par, in, r0, nval, b[3 % PF], v[3]);
+    hop_step<0, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<1, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<2, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<3, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<4, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<5, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<6, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<7, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+}
+
+// the hop of one site for NR right-hand sides, plain or pipelined
+template <typename P, int NR, bool DAG, bool PIPE>
+__device__ __forceinline__ void hop_any(const LatDev& g, const SiteX& s, int cb, int out_par, const CField<P>& in,
+                                        int r0, int nval, cpx<typename P::real> (&acc)[NR][4][3]) {
+    if constexpr (PIPE) hop_site_pipe<P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    else hop_site<P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
 }
 
 // ------------------------------------------------------------ reductions
@@ -258,40 +415,21 @@ enum FinMode {
 };
 constexpr int FIN_THREADS = 512;
 
-// Sum the block partials of each lattice (block l of this launch: rows
-// rhs * NQ + q over the lattice's blocks blk0 .. blk0 + nblk - 1, lane k
-// taking blocks k, k + 32, ... in batches of 16 independent loads, then a
-// shuffle tree: a fixed order) and apply MODE for each rhs.
-template <int NQ, typename A, int MODE, typename RV>
-__global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict__ lats, int nrhs, int nblocks,
-                                                         SolverCtx ctx, double* __restrict__ out, int maxiter) {
-    pdl_enter();
-    __shared__ double sres[MAX_RHS * 3];
-    const int l = blockIdx.x;
-    const int blk0 = lats[l].blk0, nblk = lats[l].nblk;
-    const A* __restrict__ partials = reinterpret_cast<const A*>(ctx.partials);
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = (int)blockDim.x >> 5;
-    for (int r = w; r < nrhs * NQ; r += nw) {
-        const A* src = partials + (long long)r * nblocks + blk0;
-        A a = acc_zero<A>();
-        for (int c0 = 0; c0 < nblk; c0 += 32 * 16) {
-            A v[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int c = c0 + 32 * k + lane;
-                v[k] = (c < nblk) ? acc_ldcg(src + c) : acc_zero<A>();
-            }
-#pragma unroll
-            for (int k = 0; k < 16; ++k) a = acc_add(a, v[k]);
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) a = acc_add(a, acc_shfl_down(a, off));
-        if (lane == 0) sres[r] = acc_to_double(a);
-    }
-    __syncthreads();
-    if (MODE == FIN_INIT && l == 0 && tid == 0) *ctx.loop_count = 0;
-    if (tid >= nrhs) return;
-    const int i = l * nrhs + tid;
+// The WHILE node of the iteration graph: continue while any rhs of any
+// lattice is active and the device-side cap is not reached (one thread).
+__device__ __forceinline__ void set_loop_cond(const SolverCtx& ctx, int nlat, int nrhs) {
+    int any = 0;
+    for (int i = 0; i < nlat * nrhs; ++i) any |= ctx.st[i].active;
+    const int n = atomicAdd(ctx.loop_count, 1) + 1;
+    const int go = (any && n < ctx.loop_count[1]) ? 1 : 0;
+    ctx.loop_count[2] = go;  // read by the host when the loop runs without a graph
+    if (ctx.use_cond) cudaGraphSetConditional(ctx.cond, (unsigned)go);
+}
+
+// the per-rhs effect of a reduction's lattice sums sres
+template <int MODE, typename RV>
+__device__ __forceinline__ void fin_apply(const SolverCtx& ctx, int i, int tid, const double* sres,
+                                          double* __restrict__ out, int maxiter) {
     if (MODE == FIN_NORM) {
         out[i] = sres[tid];
         return;
@@ -352,9 +490,47 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict
     }
 }
 
+// Sum the block partials of each lattice (block l of this launch: rows
+// rhs * NQ + q over the lattice's blocks blk0 .. blk0 + nblk - 1, lane k
+// taking blocks k, k + 32, ... in batches of 16 independent loads, then a
+// shuffle tree: a fixed order) and apply MODE for each rhs.
+template <int NQ, typename A, int MODE, typename RV>
+__global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict__ lats, int nrhs, int nblocks,
+                                                         SolverCtx ctx, double* __restrict__ out, int maxiter) {
+    pdl_enter();
+    __shared__ double sres[MAX_RHS * 3];
+    const int l = blockIdx.x;
+    const int blk0 = lats[l].blk0, nblk = lats[l].nblk;
+    const A* __restrict__ partials = reinterpret_cast<const A*>(ctx.partials);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = (int)blockDim.x >> 5;
+    for (int r = w; r < nrhs * NQ; r += nw) {
+        const A* src = partials + (long long)r * nblocks + blk0;
+        A a = acc_zero<A>();
+        for (int c0 = 0; c0 < nblk; c0 += 32 * 16) {
+            A v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int c = c0 + 32 * k + lane;
+                v[k] = (c < nblk) ? acc_ldcg(src + c) : acc_zero<A>();
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) a = acc_add(a, v[k]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a = acc_add(a, acc_shfl_down(a, off));
+        if (lane == 0) sres[r] = acc_to_double(a);
+    }
+    __syncthreads();
+    if (MODE == FIN_INIT && l == 0 && tid == 0) *ctx.loop_count = 0;
+    if (tid < nrhs) fin_apply<MODE, RV>(ctx, l * nrhs + tid, tid, sres, out, maxiter);
+}
+
+
+
 template <int NQ, typename A, int MODE, typename RV>
 inline void launch_finish(const LaunchCfg& c, const SolverCtx& ctx, double* out, int maxiter, cudaStream_t st) {
-    launch_pdl(k_finish<NQ, A, MODE, RV>, dim3(c.nlat), dim3(FIN_THREADS), st, c.lats, c.nrhs, c.nblocks, ctx, out, maxiter);
+    launch_pdl(k_finish<NQ, A, MODE, RV>, dim3(c.nlat), dim3(FIN_THREADS), st, c.lats, c.nrhs, c.nblocks, ctx, out,
+               maxiter);
 }
 
 template <typename R, typename A>
@@ -389,8 +565,8 @@ __device__ __forceinline__ bool rhs_active(const KState* st, int idx) { return s
 
 // ------------------------------------------------------------ kernels
 // out(out_par) = coef * H in
-template <typename PI, typename PO, int NR, bool DAG>
-__global__ void __launch_bounds__(KB<PI, NR>::MAXT, KB<PI, NR>::MINB) k_hop(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
+template <typename PI, typename PO, int NR, bool DAG, bool PIPE>
+__global__ void __launch_bounds__(KBH<PI, NR, PIPE>::MAXT, KBH<PI, NR, PIPE>::MINB) k_hop(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
                                               CField<PI> in, Field<PO> out, double coef, int kpow,
                                               const KState* __restrict__ st) {
     pdl_enter();
@@ -410,7 +586,7 @@ __global__ void __launch_bounds__(KB<PI, NR>::MAXT, KB<PI, NR>::MINB) k_hop(cons
         if (cb < 0) continue;
         const SiteX s = decode_site(g, cb, out_par);
         cpx<R> acc[NR][4][3];
-        hop_site<PI, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+        hop_any<PI, NR, DAG, PIPE>(g, s, cb, out_par, in, r0, nval, acc);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (j < nval) {
@@ -425,8 +601,8 @@ __global__ void __launch_bounds__(KB<PI, NR>::MAXT, KB<PI, NR>::MINB) k_hop(cons
 }
 
 // out(out_par) = a * xv + coef * H hin (+ zv) with a fused reduction
-template <typename PH, typename PV, int NR, bool DAG, int RED, bool HASZ>
-__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_tail(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
+template <typename PH, typename PV, int NR, bool DAG, int RED, bool HASZ, bool PIPE>
+__global__ void __launch_bounds__(KBH<PH, NR, PIPE>::MAXT, KBH<PH, NR, PIPE>::MINB) k_tail(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
                                                CField<PH> hin, CField<PV> xv, CField<PV> zv, Field<PV> out,
                                                CField<PV> ra, double a, double coef, int kpow,
                                                SolverCtx ctx) {
@@ -459,7 +635,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_tail(con
             if (cb < 0) continue;
             const SiteX s = decode_site(g, cb, out_par);
             cpx<RH> acc[NR][4][3];
-            hop_site<PH, NR, DAG>(g, s, cb, out_par, hin, r0, nval, acc);
+            hop_any<PH, NR, DAG, PIPE>(g, s, cb, out_par, hin, r0, nval, acc);
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
                 if (!act[j]) continue;
@@ -621,14 +797,7 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_p_update
             if (COPY) store_spinor<PH, RV>(ph, vbase<PH>(g, r0 + j), g.Vpad, cb, sb, pa);
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
-        int any = 0;
-        for (int i = 0; i < nlat * nrhs; ++i) any |= ctx.st[i].active;
-        const int n = atomicAdd(ctx.loop_count, 1) + 1;
-        const int go = (any && n < ctx.loop_count[1]) ? 1 : 0;
-        ctx.loop_count[2] = go;  // read by the host when the loop runs without a graph
-        if (ctx.use_cond) cudaGraphSetConditional(ctx.cond, (unsigned)go);
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) set_loop_cond(ctx, nlat, nrhs);
 }
 
 // inner start: b = r64 / |r64|; x = 0, r = r0 = p = b
@@ -775,30 +944,46 @@ inline dim3 block_of(const LaunchCfg& c) { return dim3(c.TS, (c.nrhs + c.NR - 1)
 
 template <typename PV, typename PH>
 struct OpsImpl {
+    // the pipelined hop: FP32 / FP16 operands, NR <= 2, blocks of <= 256 threads
+    static bool pipe_ok(const LaunchCfg& c) {
+        return !std::is_same<PH, P64>::value && c.NR <= 2 && c.TS * ((c.nrhs + c.NR - 1) / c.NR) <= 256;
+    }
+
+    template <int NR, bool PIPE>
+    static void hop_nr(const LaunchCfg& c, int out_par, bool dag, FieldPtr in, FieldPtr out, double coef, int kpow,
+                       const KState* ks, cudaStream_t st) {
+        if (dag)
+            launch_pdl(k_hop<PH, PH, NR, true, PIPE>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
+                       out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
+        else
+            launch_pdl(k_hop<PH, PH, NR, false, PIPE>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat,
+                       c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
+    }
+
     static cudaError_t hop(const LaunchCfg& c, int out_par, bool dag, FieldPtr in, FieldPtr out, double coef,
                            int kpow, const SolverCtx* ctx, cudaStream_t st) {
         const KState* ks = ctx ? ctx->st : nullptr;
+        if (c.pipe && !pipe_ok(c)) return cudaErrorInvalidValue;
         SF_NR_SWITCH(c.NR, {
-            if (dag)
-                launch_pdl(k_hop<PH, PH, NR_, true>, dim3(c.nblocks), dim3(block_of(c)), st, 
-                    c.lats, c.nlat, c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
-            else
-                launch_pdl(k_hop<PH, PH, NR_, false>, dim3(c.nblocks), dim3(block_of(c)), st, 
-                    c.lats, c.nlat, c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
+            if constexpr (NR_ <= 2 && !std::is_same<PH, P64>::value) {
+                if (c.pipe) hop_nr<NR_, true>(c, out_par, dag, in, out, coef, kpow, ks, st);
+                else hop_nr<NR_, false>(c, out_par, dag, in, out, coef, kpow, ks, st);
+            } else {
+                hop_nr<NR_, false>(c, out_par, dag, in, out, coef, kpow, ks, st);
+            }
         });
         return cudaGetLastError();
     }
 
-    template <int NR, bool DAG>
+    template <int NR, bool DAG, bool PIPE>
     static void tail_red(const LaunchCfg& c, int out_par, int red, FieldPtr hin, FieldPtr xv, FieldPtr zv,
                          FieldPtr out, FieldPtr ra, double a, double coef, int kpow, SolverCtx k,
                          double* norm_out, cudaStream_t st) {
         const dim3 b = block_of(c);
         const bool hz = zv.v != nullptr;
-#define SF_TAIL(RED, HZ)                                                                              \
-    launch_pdl(k_tail<PH, PV, NR, DAG, RED, HZ>, dim3(c.nblocks), dim3(b), st, c.lats, c.nlat, c.nrhs, out_par, cf<PH>(hin), \
-                                                              cf<PV>(xv), cf<PV>(zv), wf<PV>(out), cf<PV>(ra), \
-                                                              a, coef, kpow, k)
+#define SF_TAIL(RED, HZ)                                                                                        \
+    launch_pdl(k_tail<PH, PV, NR, DAG, RED, HZ, PIPE>, dim3(c.nblocks), dim3(b), st, c.lats, c.nlat, c.nrhs,  \
+               out_par, cf<PH>(hin), cf<PV>(xv), cf<PV>(zv), wf<PV>(out), cf<PV>(ra), a, coef, kpow, k)
         using A = typename AccOf<typename PV::real>::T;
         using RV = typename PV::real;
         switch (red) {
@@ -824,12 +1009,41 @@ struct OpsImpl {
                             const SolverCtx* ctx, double* norm_out, cudaStream_t st) {
         SolverCtx k{};
         if (ctx) k = *ctx;
+        if (c.pipe && !pipe_ok(c)) return cudaErrorInvalidValue;
         SF_NR_SWITCH(c.NR, {
-            if (dag) tail_red<NR_, true>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
-            else tail_red<NR_, false>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+            if constexpr (NR_ <= 2 && !std::is_same<PH, P64>::value) {
+                if (c.pipe) {
+                    if (dag) tail_red<NR_, true, true>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+                    else tail_red<NR_, false, true>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+                    break;
+                }
+            }
+            if (dag) tail_red<NR_, true, false>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+            else tail_red<NR_, false, false>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
         });
         return cudaGetLastError();
     }
+
+    // ---- one BiCGStab iteration on every rhs of every lattice: hop, tail (v,
+    // <r0,v> -> alpha), s_update, hop, tail (t, <t,s>, |t|^2 -> omega),
+    // xr_update (<r0,r>, |r|^2 -> beta, convergence), p_update (sets the loop
+    // condition): 7 kernels and the lattice sums of 3 reductions.
+    static cudaError_t iterate(const LaunchCfg& c, bool dag, const IterFields& f, const SolverCtx* ctx,
+                               cudaStream_t st) {
+        const FieldPtr none{nullptr, nullptr};
+        const bool copy = !std::is_same<PV, PH>::value;
+        cudaError_t e;
+        if ((e = hop(c, 1, dag, copy ? f.ph : f.p, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
+        if ((e = tail(c, 0, dag, RED_R0V, f.tmp, f.p, none, f.v, f.r0, 1.0, -1.0, 2, ctx, nullptr, st)) != cudaSuccess)
+            return e;
+        if ((e = s_update(c, f.r, f.v, f.s, f.sh, ctx, st)) != cudaSuccess) return e;
+        if ((e = hop(c, 1, dag, copy ? f.sh : f.s, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
+        if ((e = tail(c, 0, dag, RED_TS, f.tmp, f.s, none, f.t, none, 1.0, -1.0, 2, ctx, nullptr, st)) != cudaSuccess)
+            return e;
+        if ((e = xr_update(c, f.x, f.r, f.p, f.s, f.t, f.r0, ctx, st)) != cudaSuccess) return e;
+        return p_update(c, f.p, f.ph, f.r, f.v, ctx, st);
+    }
+    static int iteration_kernels(const LaunchCfg&) { return 10; }
 
     static cudaError_t init(const LaunchCfg& c, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
                             FieldPtr ph, const SolverCtx* ctx, int maxiter, cudaStream_t st) {
@@ -855,9 +1069,8 @@ struct OpsImpl {
     static cudaError_t xr_update(const LaunchCfg& c, FieldPtr x, FieldPtr r, FieldPtr p, FieldPtr s, FieldPtr t,
                                  FieldPtr r0, const SolverCtx* ctx, cudaStream_t st) {
         SF_NR_SWITCH(c.NR, {
-            launch_pdl(k_xr_update<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs, wf<PV>(x), wf<PV>(r),
-                                                                     cf<PV>(p), cf<PV>(s), cf<PV>(t), cf<PV>(r0),
-                                                                     *ctx);
+            launch_pdl(k_xr_update<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
+                       wf<PV>(x), wf<PV>(r), cf<PV>(p), cf<PV>(s), cf<PV>(t), cf<PV>(r0), *ctx);
         });
         launch_finish<3, typename AccOf<typename PV::real>::T, FIN_XR, typename PV::real>(c, *ctx, nullptr, 0, st);
         return cudaGetLastError();
@@ -913,6 +1126,8 @@ struct OpsImpl {
         o.unpack = &unpack;
         o.pack_h = &pack_h;
         o.unpack_h = &unpack_h;
+        o.iterate = &iterate;
+        o.iteration_kernels = &iteration_kernels;
         return o;
     }
 };

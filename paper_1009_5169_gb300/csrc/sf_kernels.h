@@ -48,6 +48,7 @@ struct LaunchCfg {
     int TS;               // sites per tile (multiple of 32)
     int NR;               // right-hand sides per thread (1, 2, 3 or 5)
     int nblocks;          // total blocks (sum of lattice nblk)
+    int pipe;             // 1: pipelined hop (FP32 / FP16, NR <= 2, TS * groups <= 256)
 };
 
 struct SolverCtx {
@@ -63,6 +64,12 @@ struct SolverCtx {
 struct FieldPtr {
     void* v;
     float* s;
+};
+
+// The vectors of the inner BiCGStab (ph, sh: hop-operand copies of p, s when
+// the hop operands are stored in another precision).
+struct IterFields {
+    FieldPtr x, r, r0, p, v, s, t, tmp, ph, sh;
 };
 
 struct KrylovOps {
@@ -92,6 +99,11 @@ struct KrylovOps {
     // the same for the hop-operand storage PH
     cudaError_t (*pack_h)(const LaunchCfg&, const double* aos, FieldPtr out, cudaStream_t);
     cudaError_t (*unpack_h)(const LaunchCfg&, FieldPtr in, double* aos, cudaStream_t);
+    // one BiCGStab iteration on every active rhs (the body of the iteration
+    // graph's WHILE node; the last kernel sets the loop condition), and the
+    // number of kernels it launches
+    cudaError_t (*iterate)(const LaunchCfg&, bool dag, const IterFields&, const SolverCtx*, cudaStream_t);
+    int (*iteration_kernels)(const LaunchCfg&);
 };
 
 // Launch a kernel of this library with programmatic stream serialization

@@ -101,28 +101,32 @@ def test_tilings_agree(sf):
     x = torch.from_numpy(inputs.sources(L, T, 5, 56)).cuda()
     outs = {}
     for prec, nrs in (("fp64", (1, 2)), ("fp32", (1, 2, 3, 5)), ("fp16", (1, 2, 3, 5))):
-        for TS in (32, 64, 128):
-            for NR in nrs:
-                RG = -(-5 // NR)
-                lim = {"fp64": 256 if NR == 1 else 128}.get(prec, 320 if NR == 1 else 384 if NR == 2 else 256)
-                if TS * RG > lim:
-                    continue
-                lat = sf.Lattice(L, T, theta, kappa, 4.52, torch.from_numpy(U).cuda())
-                lat.set_tuning(prec, TS, NR)
-                o = torch.empty_like(x)
-                sf.wilson_apply_block(lat, "dhat", prec, x, o)
-                outs.setdefault(prec, []).append(((TS, NR), o.cpu().numpy()))
-                lat.close()
+        for pipe in ((0,) if prec == "fp64" else (0, 1)):
+            for TS in (32, 64, 128):
+                for NR in nrs:
+                    RG = -(-5 // NR)
+                    lim = {"fp64": 256 if NR == 1 else 128}.get(prec, 320 if NR == 1 else 384 if NR == 2 else 256)
+                    if pipe:
+                        lim = 256 if NR <= 2 else 0
+                    if TS * RG > lim:
+                        continue
+                    lat = sf.Lattice(L, T, theta, kappa, 4.52, torch.from_numpy(U).cuda())
+                    lat.set_tuning(prec, TS, NR, pipe)
+                    assert lat.get_tuning(prec, 5) == (TS, NR, pipe)
+                    o = torch.empty_like(x)
+                    sf.wilson_apply_block(lat, "dhat", prec, x, o)
+                    outs.setdefault(prec, []).append(((TS, NR, pipe), o.cpu().numpy()))
+                    lat.close()
     for prec, lst in outs.items():
-        by_nr = {}
-        for (TS, NR), o in lst:
-            by_nr.setdefault(NR, []).append(o)
-        for NR, os_ in by_nr.items():
+        by_kernel = {}
+        for (TS, NR, pipe), o in lst:
+            by_kernel.setdefault((NR, pipe), []).append(o)
+        for key, os_ in by_kernel.items():
             for o in os_[1:]:
-                assert np.array_equal(o, os_[0]), (prec, NR)
+                assert np.array_equal(o, os_[0]), (prec, key)
         tol = {"fp64": 1e-15, "fp32": 1e-6, "fp16": 1e-6}[prec]
-        for (TS, NR), o in lst[1:]:
-            assert relerr(o, lst[0][1]) <= tol, (prec, TS, NR)
+        for (TS, NR, pipe), o in lst[1:]:
+            assert relerr(o, lst[0][1]) <= tol, (prec, TS, NR, pipe)
 
 
 def test_host_and_device_pointers_agree(sf):
@@ -259,11 +263,15 @@ def test_set_links_updates_every_precision(sf):
 def test_tiling_validation(sf):
     """Unsupported tilings are refused with SF_EINVAL, nothing launched."""
     U, lat = _lattice(sf, 4, 4, 0.3, 0.125, 0.5)
-    for prec, TS, NR in (("fp32", 96, 1), ("fp16", 64, 4), ("fp64", 48, 1), ("fp64", 32, 3)):
+    for prec, TS, NR, pipe in (("fp32", 96, 1, 0), ("fp16", 64, 4, 0), ("fp64", 48, 1, 0), ("fp64", 32, 3, 0),
+                               ("fp64", 32, 1, 1), ("fp32", 32, 3, 1), ("fp32", 32, 1, 2)):
         with pytest.raises(sf.SFError):
-            lat.set_tuning(prec, TS, NR)
+            lat.set_tuning(prec, TS, NR, pipe)
     lat.set_tuning("fp64", 128, 2)   # 128 x 3 rhs groups > 128 threads at NR = 2
     x = torch.from_numpy(inputs.sources(4, 4, 5, 3)).cuda()
     with pytest.raises(sf.SFError):
         sf.wilson_apply_block(lat, "dhat", "fp64", x, torch.empty_like(x))
+    lat.set_tuning("fp32", 128, 2, 1)   # pipelined: 128 x 3 > 256 threads
+    with pytest.raises(sf.SFError):
+        sf.wilson_apply_block(lat, "dhat", "fp32", x, torch.empty_like(x))
     lat.close()
