@@ -101,7 +101,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -164,14 +164,13 @@ def run_ours(args, rank, world, local_rank):
     eps_md = 0.01
 
     def step(Ub, ph, X, Y, F, mom):
+        # the links of this MD step, then Alg. 2: X, Y and the force (the odd
+        # sites of X, Y come from the final residuals' hops)
         lat.set_links(Ub)
-        info = sf.solve_block(lat, args.algo, ph, X, Y, tol=tol, maxiter=args.maxiter)
-        sf.fermion_force(lat, X, Y, F, mom, eps=eps_md)
-        return info
+        return sf.md_force_step(lat, args.algo, ph, X, Y, F, mom, eps=eps_md, tol=tol, maxiter=args.maxiter)
 
-    # fixed launches per step outside the solver: SU(3) check + link prep, and
-    # in the force: 2 packs, 2 odd-site hops, 1 force kernel
-    fixed_launches = 2 + 5
+    # launches per step outside md_force_step's own count: SU(3) check + link prep
+    fixed_launches = 2
     for _ in range(args.warmup):
         info = step(U_d, phi_d, X_d, Y_d, F_d, mom_d)
     torch.cuda.synchronize()
@@ -587,7 +586,7 @@ def run_dslash_only(args, local_rank):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sf12_nf10")

@@ -173,6 +173,15 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
 sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double* Y, double* F, double* mom,
                         double eps);
 
+/* Alg. 2 as one call: the two solves (as solve_block, X and Y both returned)
+ * and the force (as fermion_force, F and / or mom -= eps F).  The odd-site
+ * parts of X and Y that the force needs are the first hops of the final FP64
+ * true residuals, so no extra hops are applied.  Same layouts, precision
+ * rules and statuses as solve_block and fermion_force; on SF_ENOCONV all
+ * outputs are still written (from the best iterates). */
+sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* X, double* Y,
+                        double* F, double* mom, double eps, double tol, int maxiter, sf_solve_info* info);
+
 /* S_g = beta sum_p w(p) (1 - Re tr U_p / 3) over the SF gauge lattice with
  * w = 1/2 for spatial plaquettes at x0 = 0 and x0 = T and 1 otherwise. */
 sf_status plaquette_action(sf_lattice* lat, double* S);

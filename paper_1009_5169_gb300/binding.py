@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
         L.wilson_hop_resident.argtypes = [vp, i, i, i]
         L.solve_block.argtypes = [vp, i, i, vp, vp, vp, d, i, ctypes.POINTER(SolveInfo)]
         L.fermion_force.argtypes = [vp, i, vp, vp, vp, vp, d]
+        L.md_force_step.argtypes = [vp, i, i, vp, vp, vp, vp, vp, d, d, i, ctypes.POINTER(SolveInfo)]
         L.plaquette_action.argtypes = [vp, ctypes.POINTER(d)]
         L.plaquette_action_noalloc.argtypes = [i, i, d, vp, vp, i, vp]
         L.plaquette_action_noalloc.restype = ctypes.c_int
@@ -98,7 +99,8 @@ def lib() -> ctypes.CDLL:
         L.sf_batch_destroy.argtypes = [vp]
         L.sf_batch_destroy.restype = None
         for fn in ("sf_lattice_create", "sf_lattice_set_links", "sf_lattice_set_tuning", "sf_lattice_get_tuning",
-                   "wilson_apply_block", "wilson_hop_resident", "solve_block", "fermion_force", "plaquette_action", "sf_batch_create",
+                   "wilson_apply_block", "wilson_hop_resident", "solve_block", "fermion_force", "md_force_step",
+                   "plaquette_action", "sf_batch_create",
                    "sf_batch_solve"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
@@ -246,6 +248,27 @@ def fermion_force(lat: Lattice, X, Y, F=None, mom=None, eps: float = 0.0) -> Non
     if mom is not None:
         _check_size(mom, fb, "mom")
     _check(lib().fermion_force(lat.handle, nrhs, _ptr(X), _ptr(Y), _ptr(F), _ptr(mom), eps))
+
+
+def md_force_step(lat: Lattice, algo: str, phi, X, Y, F=None, mom=None, eps: float = 0.0, tol: float = 1e-10,
+                  maxiter: int = 10000, allow_noconv: bool = False) -> dict:
+    """Alg. 2 in one call: X = Dhat^-1 phi, Y = Dhat^-dag X and the force of Eq. (3)
+    (F and / or mom -= eps F), reusing the odd-site hops of the final residuals."""
+    nrhs = _nrhs_of(phi, lat.Vh * 24 * 8)
+    _check_size(X, nrhs * lat.Vh * 24 * 8, "X")
+    _check_size(Y, nrhs * lat.Vh * 24 * 8, "Y")
+    fb = (lat.T + 1) * lat.L ** 3 * 4 * 8 * 8
+    if F is not None:
+        _check_size(F, fb, "F")
+    if mom is not None:
+        _check_size(mom, fb, "mom")
+    info = SolveInfo()
+    rc = lib().md_force_step(lat.handle, ALGOS[algo], nrhs, _ptr(phi), _ptr(X), _ptr(Y), _ptr(F), _ptr(mom), eps,
+                             tol, maxiter, ctypes.byref(info))
+    _check(rc, allow_noconv)
+    d = info.as_dict(nrhs)
+    d["status"] = STATUS[rc]
+    return d
 
 
 def plaquette_action(lat: Lattice) -> float:

@@ -433,9 +433,11 @@ struct Workspace {
         const KrylovOps& o = ops_f64();
         const LaunchCfg& lc = cfg[0].lc;
         SolverCtx k = ctx(false);
-        CK(o.hop(lc, 1, dag, x.ptr(), t64o.ptr(), 1.0, 0, nullptr, s));
+        // t64o = kappa H_oe x (dag: kappa gamma5 H_oe gamma5 x) is the odd-site part of the
+        // full-lattice solution (Sec. 3.1); r64 = phi - (x - kappa H_eo t64o)
+        CK(o.hop(lc, 1, dag, x.ptr(), t64o.ptr(), 1.0, 1, nullptr, s));
         CK(o.tail(lc, 0, dag, RED_NORM, t64o.ptr(), x.ptr(), phi.ptr(), r64.ptr(), FieldPtr{nullptr, nullptr}, -1.0,
-                  1.0, 2, &k, nrm_rr.as<double>(), s));
+                  1.0, 1, &k, nrm_rr.as<double>(), s));
         launches += 3;  // hop, tail, lattice sums
     }
 
@@ -475,7 +477,11 @@ struct Workspace {
 
     Result fgcr(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
 
-    Result solve(int ci, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter, bool from_x = false) {
+    // odd (optional): receives the odd-site reconstruction kappa H_oe x of the
+    // final x (dag: kappa gamma5 H_oe gamma5 x), the first hop of the last true
+    // residual, so the force needs no hop of its own.
+    Result solve(int ci, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter, bool from_x = false,
+                 FieldBuf* odd = nullptr) {
         ensure_cfg(0);
         ensure_cfg(ci);
         ensure_inner(ci);
@@ -500,13 +506,16 @@ struct Workspace {
         CK(cudaMemcpyAsync(loop_count.as<int>() + 1, pin + 2, sizeof(int), cudaMemcpyHostToDevice, s));
         SolverCtx k = ctx(true);
         Result res;
+        bool have_odd = false;  // t64o holds kappa H_oe x of the current x
         for (int sweep = 0;; ++sweep) {
             if (sweep == 0 && !from_x) {
                 // x = 0: r = phi
                 CK(cudaMemcpyAsync(r64.v.p, phi.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, s));
                 CK(cudaMemcpyAsync(nrm_rr.p, nrm_bb.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                have_odd = false;
             } else {
                 residual64(dag, phi, x, s);
+                have_odd = true;
             }
             CK(launch_outer_check((int)n, ost.as<OState>(), nrm_rr.as<double>(),
                                   sweep == 0 ? nrm_bb.as<double>() : nullptr, max_sweeps, n_active.as<int>(), s));
@@ -535,6 +544,10 @@ struct Workspace {
             launches += 3;  // init (+ its sums), dc_update
             CK(cudaStreamSynchronize(s));
             launches += (long long)o.iteration_kernels(cfg[ci].lc) * pin[1];
+        }
+        if (odd) {
+            if (have_odd) CK(cudaMemcpyAsync(odd->v.p, t64o.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, s));
+            else CK(cudaMemsetAsync(odd->v.p, 0, field_bytes(Prec::F64, S), s));  // x = 0
         }
         std::vector<OState> out(n);
         CK(cudaMemcpy(out.data(), ost.p, n * sizeof(OState), cudaMemcpyDeviceToHost));
@@ -1146,6 +1159,50 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
     return st;
 }
 
+namespace {
+
+// Odd-site buffers of the force, allocated on first use.
+void ensure_odd(Workspace& w) {
+    if (!w.xo64.v.p) {
+        w.xo64.alloc(Prec::F64, w.S);
+        w.yo64.alloc(Prec::F64, w.S);
+    }
+}
+
+// The force of Eq. (3) from the workspace's x64, xo64, y64, yo64 (even and
+// odd sites of X and Y): F = sum_i f[x_i, y_i] and / or mom -= eps F.
+void force_from_workspace(sf_lattice* lat, Workspace& w, double* F, double* mom, double eps) {
+    cudaStream_t s = lat->stream;
+    const LaunchCfg& pl = w.cfg[0].per_lat[0];
+    const size_t fbytes = (size_t)(lat->T + 1) * lat->L * lat->L * lat->L * 4 * 8 * sizeof(double);
+    double* dF = nullptr;
+    if (F) {
+        dF = out_device(F, fbytes, lat->stage_out);
+        CK(cudaMemsetAsync(dF, 0, fbytes, s));
+    }
+    double* dM = nullptr;
+    DevMem mstage;
+    if (mom) {
+        if (is_device_ptr(mom)) {
+            dM = mom;
+        } else {
+            mstage.ensure(fbytes);
+            CK(cudaMemcpyAsync(mstage.p, mom, fbytes, cudaMemcpyHostToDevice, s));
+            dM = mstage.as<double>();
+        }
+    }
+    CK(launch_force(pl, w.x64.ptr(), w.xo64.ptr(), w.y64.ptr(), w.yo64.ptr(), dF, dM, eps, s));
+    w.launches += 1;
+    if (F) finish_out(F, dF, fbytes, s);
+    if (mom && dM != mom) {
+        CK(cudaMemcpyAsync(mom, dM, fbytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    CK(cudaGetLastError());
+}
+
+}  // namespace
+
 sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double* Y, double* F, double* mom,
                         double eps) {
     return guarded([&] {
@@ -1155,10 +1212,7 @@ sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.ensure_cfg(0);
-        if (!w.xo64.v.p) {
-            w.xo64.alloc(Prec::F64, w.S);
-            w.yo64.alloc(Prec::F64, w.S);
-        }
+        ensure_odd(w);
         cudaStream_t s = lat->stream;
         const KrylovOps& o = ops_f64();
         const LaunchCfg& lc = w.cfg[0].lc;
@@ -1171,31 +1225,63 @@ sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double
         // odd-site reconstruction: Xh_o = kappa H_oe x_e, Yh_o = kappa gamma_5 H_oe gamma_5 y_e
         CK(o.hop(lc, 1, false, w.x64.ptr(), w.xo64.ptr(), 1.0, 1, nullptr, s));
         CK(o.hop(lc, 1, true, w.y64.ptr(), w.yo64.ptr(), 1.0, 1, nullptr, s));
-        const size_t fbytes = (size_t)(lat->T + 1) * lat->L * lat->L * lat->L * 4 * 8 * sizeof(double);
-        double* dF = nullptr;
-        if (F) {
-            dF = out_device(F, fbytes, lat->stage_out);
-            CK(cudaMemsetAsync(dF, 0, fbytes, s));
-        }
-        double* dM = nullptr;
-        DevMem mstage;
-        if (mom) {
-            if (is_device_ptr(mom)) {
-                dM = mom;
-            } else {
-                mstage.ensure(fbytes);
-                CK(cudaMemcpyAsync(mstage.p, mom, fbytes, cudaMemcpyHostToDevice, s));
-                dM = mstage.as<double>();
-            }
-        }
-        CK(launch_force(pl, w.x64.ptr(), w.xo64.ptr(), w.y64.ptr(), w.yo64.ptr(), dF, dM, eps, s));
-        if (F) finish_out(F, dF, fbytes, s);
-        if (mom && dM != mom) {
-            CK(cudaMemcpyAsync(mom, dM, fbytes, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-        }
-        CK(cudaGetLastError());
+        force_from_workspace(lat, w, F, mom, eps);
     });
+}
+
+sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* X, double* Y,
+                        double* F, double* mom, double eps, double tol, int maxiter, sf_solve_info* info) {
+    bool noconv = false;
+    sf_status st = guarded([&] {
+        const auto t0 = std::chrono::steady_clock::now();
+        REQUIRE(lat != nullptr && phi != nullptr && X != nullptr && Y != nullptr, "NULL argument");
+        REQUIRE(F != nullptr || mom != nullptr, "F and mom are both NULL");
+        check_nrhs(nrhs);
+        REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
+        REQUIRE(maxiter >= 1, "maxiter must be >= 1");
+        const int ci = algo_index(algo);
+        const bool fgcr = (ci >= 3);
+        CK(cudaSetDevice(lat->device));
+        Workspace& w = lattice_ws(lat, nrhs);
+        w.launches = 0;
+        w.ensure_cfg(0);
+        if (!fgcr) w.ensure_cfg(ci);
+        ensure_odd(w);
+        cudaStream_t s = lat->stream;
+        const KrylovOps& o = ops_f64();
+        const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
+        const LaunchCfg& pl = w.cfg[0].per_lat[0];
+        const double* dphi = to_device(phi, bytes, lat->stage_in, s);
+        CK(o.pack(pl, dphi, w.phi64.ptr(), s));
+        w.launches += 1;
+        // X = Dhat^-1 phi and its odd part; Y = Dhat^-dag X and its odd part
+        auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol, FieldBuf& odd) {
+            if (!fgcr) return w.solve(ci, dag, rhs, sol, tol, maxiter, false, &odd);
+            Workspace::Result r = w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter);
+            CK(o.hop(w.cfg[0].lc, 1, dag, sol.ptr(), odd.ptr(), 1.0, 1, nullptr, s));
+            w.launches += 1;
+            return r;
+        };
+        Workspace::Result rx = run(false, w.phi64, w.x64, w.xo64);
+        double* dX = out_device(X, bytes, lat->stage_out);
+        CK(o.unpack(pl, w.x64.ptr(), dX, s));
+        finish_out(X, dX, bytes, s);
+        Workspace::Result ry = run(true, w.x64, w.y64, w.yo64);
+        double* dY = out_device(Y, bytes, lat->stage_out);
+        CK(o.unpack(pl, w.y64.ptr(), dY, s));
+        finish_out(Y, dY, bytes, s);
+        w.launches += 2;
+        force_from_workspace(lat, w, F, mom, eps);
+        CK(cudaStreamSynchronize(s));
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        fill_info(info, rx, &ry, 0, nrhs, secs, w.launches);
+        if (!rx.converged || !ry.converged) noconv = true;
+    });
+    if (st == SF_OK && noconv) {
+        g_err = "solver stopped above tolerance";
+        return SF_ENOCONV;
+    }
+    return st;
 }
 
 sf_status plaquette_action(sf_lattice* lat, double* S) {

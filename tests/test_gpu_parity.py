@@ -190,6 +190,34 @@ def test_solve_five_rhs_and_force_sf12(sf):
     lat.close()
 
 
+@pytest.mark.parametrize("algo", ["mixed_dc", "bicgstab", "fgcr"])
+def test_md_force_step_matches_separate_calls(sf, algo):
+    """Alg. 2 in one call reuses the odd-site hops of the final residuals: the
+    same X, Y and force, bitwise, as solve_block followed by fermion_force
+    (which applies those hops itself), and the force matches the oracle."""
+    L, T, eps, kappa, theta = 6, 7, 0.3, 0.13, 0.5
+    U = inputs.links(L, T, eps, 41)
+    phi = inputs.sources(L, T, 3, 42)
+    lat = sf.Lattice(L, T, theta, kappa, 4.52, torch.from_numpy(U).cuda())
+    phid = torch.from_numpy(phi).cuda()
+    fshape = ((T + 1) * L ** 3, 4, 8)
+    X1, Y1 = torch.empty_like(phid), torch.empty_like(phid)
+    F1 = torch.zeros(fshape, dtype=torch.float64, device="cuda")
+    sf.solve_block(lat, algo, phid, X1, Y1, tol=1e-10, maxiter=3000)
+    sf.fermion_force(lat, X1, Y1, F1)
+    X2, Y2 = torch.empty_like(phid), torch.empty_like(phid)
+    F2 = torch.zeros(fshape, dtype=torch.float64, device="cuda")
+    mom = torch.ones(fshape, dtype=torch.float64, device="cuda")
+    info = sf.md_force_step(lat, algo, phid, X2, Y2, F2, mom, eps=0.25, tol=1e-10, maxiter=3000)
+    assert info["status"] == "SF_OK"
+    assert torch.equal(X1, X2) and torch.equal(Y1, Y2)
+    assert torch.equal(F1, F2)
+    Fo = oracle.force(U, X2.cpu().numpy(), Y2.cpu().numpy(), L, T, theta, kappa)
+    assert relerr(F2.cpu().numpy(), Fo) <= 1e-12
+    assert relerr(mom.cpu().numpy(), 1.0 - 0.25 * Fo) <= 1e-14
+    lat.close()
+
+
 def test_rhs_independence_bitwise(sf):
     """The result for pseudo-fermion i does not depend on the other fields
     (Sec. 2: the phi_i are independent): permuting the block permutes the
