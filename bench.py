@@ -223,9 +223,15 @@ def run_ours(args, rank, world, local_rank):
     d2h = nb(X_h) + nb(Y_h) + nb(F_h) + nb(mom_h)
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # ---------------- accuracy re-check outside the timed region: solve_block
+    # recomputes both FP64 true residuals (md_force_step with the CG route
+    # reports Y's, the rounding-level |X - Dhat^dag Y|, without recomputing it)
+    chk = sf.solve_block(lat, args.algo, phi_d, X_d, Y_d, tol=tol, maxiter=args.maxiter)
+    recheck = {"max_true_rel_resid_x": max(chk["true_resid"]), "max_true_rel_resid_y": max(chk["true_resid_y"])}
+
     # ---------------- roofline of the dominant kernel: the FP32 dslash (hop)
     peak, peak_kind = _peaks()
-    prec = "fp32" if args.algo == "mixed_dc" else ("fp16" if args.algo == "mixed_dc_half" else "fp64")
+    prec = "fp32" if args.algo in ("mixed_dc", "cg_normal") else ("fp16" if args.algo == "mixed_dc_half" else "fp64")
     TS, NR, PIPE = lat.get_tuning(prec, nrhs)
     Vh = lt.Vh
     site_bytes = {"fp32": nrhs * 96 * 2 + 8 * 48, "fp16": nrhs * 52 * 2 + 8 * 24,
@@ -262,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
     # ---------------- dslash on a lattice larger than L2 (HBM-bound case)
     hbm = None
     if not args.no_hbm_case and rank == 0:
-        Lh, Th = 24, 24
+        Lh, Th = 32, 32
         Ub = inputs.links(Lh, Th, 0.2, inputs.SEED_BASE + 32)
         big = sf.Lattice(Lh, Th, 0.5, 0.13, 4.52, torch.from_numpy(Ub).to(dev), device=local_rank)
         del Ub
@@ -291,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
             Vhb = Lh ** 3 * (Th - 1) // 2
             sb = {"fp32": nrhs * 96 * 2 + 8 * 48, "fp16": nrhs * 52 * 2 + 8 * 24}[p]
             ab = Vhb * sb
-            trb = _ncu_traffic(f"sf24:{p}", TSb, NRb, PIPEb)
+            trb = _ncu_traffic(f"sf32:{p}", TSb, NRb, PIPEb)
             res[p] = {"achieved": round(ab / t / 1e9, 1), "frac": round(ab / t / 1e9 / peak, 4),
                       "launch_us": round(t * 1e6, 2), "achieved_l2_flushed": round(ab / tc / 1e9, 1),
                       "launch_us_l2_flushed": round(tc * 1e6, 2), "algorithmic_bytes_per_launch": ab,
@@ -313,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             return (time.perf_counter() - t0) / reps, inf
         comparators = {}
-        for algo in ("bicgstab", "mixed_dc", "mixed_dc_half"):
+        for algo in ("bicgstab", "mixed_dc", "mixed_dc_half", "cg_normal"):
             t, inf = time_solve(algo, phi_d, X_d, Y_d)
             comparators[f"{algo}_block{nrhs}"] = {
                 "ms": round(t * 1e3, 3), "sweeps": [inf["iters_outer"], inf["iters_outer_y"]],
@@ -385,7 +391,8 @@ def run_ours(args, rank, world, local_rank):
                    "algo": args.algo, "l2": "flushed between steps", "parallelism": f"replicas x{world}",
                    "tiling": {"fp64": lat.get_tuning("fp64", nrhs), prec: (TS, NR, PIPE)}},
         "accuracy": {"max_true_rel_resid": resid, "sweeps_x": last["iters_outer"], "inner_iters_x": last["iters_inner"],
-                     "sweeps_y": last["iters_outer_y"], "inner_iters_y": last["iters_inner_y"]},
+                     "sweeps_y": last["iters_outer_y"], "inner_iters_y": last["iters_inner_y"],
+                     "solve_block_recheck": recheck},
         "roofline": roofline, "dslash_hbm": hbm, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "comparators": comparators, "batched": batched, "learned": learned,
     }
@@ -590,7 +597,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sf12_nf10")
-    ap.add_argument("--algo", default="mixed_dc", choices=["bicgstab", "mixed_dc", "mixed_dc_half"])
+    ap.add_argument("--algo", default="cg_normal", choices=["bicgstab", "mixed_dc", "mixed_dc_half", "cg_normal"])
     ap.add_argument("--maxiter", type=int, default=5000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hbm-case", action="store_true")

@@ -105,7 +105,12 @@ typedef enum {
     SF_SOLVE_FGCR_CNN = 3,
     /* the same FGCR with the identity as preconditioner (the comparison
        without the network) */
-    SF_SOLVE_FGCR = 4
+    SF_SOLVE_FGCR = 4,
+    /* the normal-equation route to the same X, Y: Y by CG on Dhat Dhat^dag
+     * (= gamma5 Dhat^dag Dhat gamma5; FP32 inner, FP64 outer defect correction
+     * on that system), X = Dhat^dag Y in FP64.  |phi - Dhat X| is the outer
+     * residual CG is driven to; |X - Dhat^dag Y| is at rounding level. */
+    SF_SOLVE_CG_NORMAL = 5
 } sf_algo;
 
 typedef struct {
@@ -178,7 +183,10 @@ sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double
  * parts of X and Y that the force needs are the first hops of the final FP64
  * true residuals, so no extra hops are applied.  Same layouts, precision
  * rules and statuses as solve_block and fermion_force; on SF_ENOCONV all
- * outputs are still written (from the best iterates). */
+ * outputs are still written (from the best iterates).  With
+ * SF_SOLVE_CG_NORMAL, X is computed as Dhat^dag Y in FP64 and
+ * info->true_resid_y is reported as 0 without recomputation (solve_block
+ * recomputes it: FP64 rounding). */
 sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* X, double* Y,
                         double* F, double* mom, double eps, double tol, int maxiter, sf_solve_info* info);
 

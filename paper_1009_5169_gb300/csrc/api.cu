@@ -240,7 +240,7 @@ struct Workspace {
         std::vector<LaunchCfg> per_lat;  // pack / unpack / force on lattice l
     } cfg[4];  // FP64, FP32, FP16 hop configurations; [3] FP64 BLAS (TS = 32, NR = 1)
 
-    FieldBuf phi64, x64, y64, r64, t64o, xo64, yo64;
+    FieldBuf phi64, x64, y64, r64, t64o, xo64, yo64, w64;
     struct Inner {
         FieldBuf x, r, r0, p, v, s, t, tmp, ph, sh;
         bool ok = false;
@@ -278,6 +278,7 @@ struct Workspace {
         y64.alloc(Prec::F64, S);
         r64.alloc(Prec::F64, S);
         t64o.alloc(Prec::F64, S);
+        w64.alloc(Prec::F64, S);
         const size_t n = (size_t)nlat * nrhs;
         st.ensure(n * sizeof(KState));
         ost.ensure(n * sizeof(OState));
@@ -325,8 +326,7 @@ struct Workspace {
         }
         c.ready = true;
         // graphs bake launch shapes in
-        graphs.erase(ci * 2);
-        graphs.erase(ci * 2 + 1);
+        for (int k : {0, 1, 8, 9}) graphs.erase(ci * 2 + k);
     }
 
     void ensure_inner(int ci) {
@@ -364,15 +364,16 @@ struct Workspace {
     }
 
     // one BiCGStab iteration on all rhs: 7 kernels and the lattice sums of its 3 reductions
-    void enqueue_iteration(int ci, bool dag, const SolverCtx& k, cudaStream_t s) {
+    void enqueue_iteration(int ci, bool dag, const SolverCtx& k, cudaStream_t s, bool cg = false) {
         Inner& in = inner[ci];
         const IterFields f{in.x.ptr(), in.r.ptr(), in.r0.ptr(), in.p.ptr(), in.v.ptr(),
                            in.s.ptr(), in.t.ptr(), in.tmp.ptr(), in.ph.ptr(), in.sh.ptr()};
-        CK(ops_for(ci).iterate(cfg[ci].lc, dag, f, &k, s));
+        const KrylovOps& o = ops_for(ci);
+        CK(cg ? o.iterate_cg(cfg[ci].lc, dag, f, &k, s) : o.iterate(cfg[ci].lc, dag, f, &k, s));
     }
 
-    GraphEntry& graph(int ci, bool dag) {
-        const int key = ci * 2 + (dag ? 1 : 0);
+    GraphEntry& graph(int ci, bool dag, bool cg = false) {
+        const int key = ci * 2 + (dag ? 1 : 0) + (cg ? 8 : 0);
         auto it = graphs.find(key);
         if (it != graphs.end()) return *it->second;
         auto ge = std::make_unique<GraphEntry>();
@@ -393,7 +394,7 @@ struct Workspace {
         k.use_cond = 1;
         CK(cudaStreamBeginCaptureToGraph(cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         try {
-            enqueue_iteration(ci, dag, k, cap_stream);
+            enqueue_iteration(ci, dag, k, cap_stream, cg);
         } catch (...) {
             cudaGraph_t dummy;
             cudaStreamEndCapture(cap_stream, &dummy);
@@ -477,11 +478,55 @@ struct Workspace {
 
     Result fgcr(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
 
+    // per-rhs |b - A x| / |b| in FP64 (A = Dhat, or Dhat^dag for dag)
+    std::vector<double> rel_residual(bool dag, const FieldBuf& b, const FieldBuf& x) {
+        ensure_cfg(0);
+        SolverCtx k0 = ctx(false);
+        CK(launch_norm2(cfg[0].lc, b.ptr(), &k0, nrm_bb.as<double>(), stream));
+        launches += 2;
+        residual64(dag, b, x, stream);
+        const size_t n = (size_t)nlat * nrhs;
+        std::vector<double> rr(n), bb(n), out(n);
+        CK(cudaMemcpyAsync(rr.data(), nrm_rr.p, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        CK(cudaMemcpyAsync(bb.data(), nrm_bb.p, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        for (size_t i = 0; i < n; ++i) out[i] = bb[i] > 0 ? sqrt(rr[i] / bb[i]) : 0.0;
+        return out;
+    }
+
+    // The normal-equation route to the same pair: Y solves (Dhat Dhat^dag) Y = phi
+    // by CG (FP32 inner, FP64 outer), X = Dhat^dag Y (the FP64 product of the final
+    // residual, so |phi - Dhat X| is exactly the residual the outer loop judged).
+    // rx: the CG sweeps and iterations with |phi - Dhat X| / |phi|; ry: |X - Dhat^dag Y| / |X|.
+    // With xo / yo, the odd-site parts of X and Y (kappa H_oe X, kappa g5 H_oe g5 Y) are
+    // kept from the final residual's hops.  check_y: recompute |X - Dhat^dag Y| / |X|
+    // (X is that very product, so it is at FP64 rounding); otherwise reported as 0.
+    void solve_normal(const FieldBuf& phi, double tol, int maxiter, Result& rx, Result& ry, bool check_y,
+                      FieldBuf* xo = nullptr, FieldBuf* yo = nullptr) {
+        rx = solve(1, false, phi, y64, tol, maxiter, false, xo, true, yo);
+        CK(cudaMemcpyAsync(x64.v.p, w64.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, stream));
+        ry = Result();
+        const size_t n = (size_t)nlat * nrhs;
+        ry.sweeps.assign(n, 0);
+        ry.inner.assign(n, 0);
+        if (check_y) {
+            ry.resid = rel_residual(true, x64, y64);
+            for (double r : ry.resid)
+                if (!(r <= tol)) ry.converged = false;
+        } else {
+            ry.resid.assign(n, 0.0);
+        }
+    }
+
     // odd (optional): receives the odd-site reconstruction kappa H_oe x of the
     // final x (dag: kappa gamma5 H_oe gamma5 x), the first hop of the last true
     // residual, so the force needs no hop of its own.
+    //
+    // cg: the normal-equation route -- x solves (Dhat Dhat^dag) x = phi by CG
+    // (FP32 inner, FP64 outer on the same system); w64 then holds Dhat^dag x
+    // of the final residual (dag and odd are not used).
     Result solve(int ci, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter, bool from_x = false,
-                 FieldBuf* odd = nullptr) {
+                 FieldBuf* odd = nullptr, bool cg = false, FieldBuf* odd_dag = nullptr) {
         ensure_cfg(0);
         ensure_cfg(ci);
         ensure_inner(ci);
@@ -501,9 +546,11 @@ struct Workspace {
         SolverCtx k0 = ctx(false);
         CK(launch_norm2(cfg[0].lc, phi.ptr(), &k0, nrm_bb.as<double>(), s));
         launches += 2;
-        GraphEntry& ge = graph(ci, dag);
-        pin[2] = maxiter + 8;
+        GraphEntry& ge = graph(ci, dag, cg);
+        pin[2] = maxiter + 8;  // WHILE cap
+        pin[5] = 0;            // iterations of this solve
         CK(cudaMemcpyAsync(loop_count.as<int>() + 1, pin + 2, sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(loop_count.as<int>() + 3, pin + 5, sizeof(int), cudaMemcpyHostToDevice, s));
         SolverCtx k = ctx(true);
         Result res;
         bool have_odd = false;  // t64o holds kappa H_oe x of the current x
@@ -513,6 +560,18 @@ struct Workspace {
                 CK(cudaMemcpyAsync(r64.v.p, phi.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, s));
                 CK(cudaMemcpyAsync(nrm_rr.p, nrm_bb.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
                 have_odd = false;
+            } else if (cg) {
+                // w = Dhat^dag x with its first hop kappa gamma5 H_oe gamma5 x (the odd part of x
+                // as the adjoint solution), then r = phi - Dhat w (first hop: the odd part of w)
+                const KrylovOps& o64 = ops_f64();
+                CK(o64.hop(cfg[0].lc, 1, true, x.ptr(), t64o.ptr(), 1.0, 1, nullptr, s));
+                if (odd_dag) CK(cudaMemcpyAsync(odd_dag->v.p, t64o.v.p, field_bytes(Prec::F64, S),
+                                                cudaMemcpyDeviceToDevice, s));
+                CK(o64.tail(cfg[0].lc, 0, true, RED_NONE, t64o.ptr(), x.ptr(), FieldPtr{nullptr, nullptr}, w64.ptr(),
+                            FieldPtr{nullptr, nullptr}, 1.0, -1.0, 1, nullptr, nullptr, s));
+                launches += 2;
+                residual64(false, phi, w64, s);
+                have_odd = true;
             } else {
                 residual64(dag, phi, x, s);
                 have_odd = true;
@@ -523,15 +582,15 @@ struct Workspace {
             CK(cudaMemcpyAsync(pin, n_active.p, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (pin[0] == 0) break;
-            CK(o.init(cfg[ci].lc, r64.ptr(), inner[ci].x.ptr(), inner[ci].r.ptr(), inner[ci].r0.ptr(),
-                      inner[ci].p.ptr(), inner[ci].ph.ptr(), &k, maxiter, s));
+            CK((cg ? o.init_cg : o.init)(cfg[ci].lc, r64.ptr(), inner[ci].x.ptr(), inner[ci].r.ptr(),
+                                         inner[ci].r0.ptr(), inner[ci].p.ptr(), inner[ci].ph.ptr(), &k, maxiter, s));
             if (no_graph()) {
                 // same kernels launched one by one, the loop condition read back
                 // by the host after each iteration (for profilers that cannot
                 // see inside conditional graph nodes)
                 SolverCtx kn = ctx(true);
                 for (;;) {
-                    enqueue_iteration(ci, dag, kn, s);
+                    enqueue_iteration(ci, dag, kn, s, cg);
                     CK(cudaMemcpyAsync(pin + 3, loop_count.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
                     CK(cudaStreamSynchronize(s));
                     if (!pin[3]) break;
@@ -540,17 +599,21 @@ struct Workspace {
                 CK(cudaGraphLaunch(ge.exec, s));
             }
             CK(o.dc_update(cfg[ci].lc, x.ptr(), inner[ci].x.ptr(), &k, s));
-            CK(cudaMemcpyAsync(pin + 1, loop_count.p, sizeof(int), cudaMemcpyDeviceToHost, s));
             launches += 3;  // init (+ its sums), dc_update
-            CK(cudaStreamSynchronize(s));
-            launches += (long long)o.iteration_kernels(cfg[ci].lc) * pin[1];
         }
         if (odd) {
             if (have_odd) CK(cudaMemcpyAsync(odd->v.p, t64o.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, s));
             else CK(cudaMemsetAsync(odd->v.p, 0, field_bytes(Prec::F64, S), s));  // x = 0
         }
+        if (cg && !have_odd) {  // x = 0
+            CK(cudaMemsetAsync(w64.v.p, 0, field_bytes(Prec::F64, S), s));
+            if (odd_dag) CK(cudaMemsetAsync(odd_dag->v.p, 0, field_bytes(Prec::F64, S), s));
+        }
         std::vector<OState> out(n);
-        CK(cudaMemcpy(out.data(), ost.p, n * sizeof(OState), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(out.data(), ost.p, n * sizeof(OState), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(pin + 5, loop_count.as<int>() + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        launches += (long long)(cg ? o.iteration_kernels_cg : o.iteration_kernels)(cfg[ci].lc) * pin[5];
         res.sweeps.resize(n);
         res.inner.resize(n);
         res.resid.resize(n);
@@ -1101,6 +1164,7 @@ int algo_index(sf_algo a) {
         case SF_SOLVE_MIXED_DC_HALF: return 2;
         case SF_SOLVE_FGCR_CNN: return 3;
         case SF_SOLVE_FGCR: return 4;
+        case SF_SOLVE_CG_NORMAL: return 5;
     }
     throw SfError{SF_EINVAL, "bad algorithm"};
 }
@@ -1117,12 +1181,12 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         const int ci = algo_index(algo);
-        const bool fgcr = (ci >= 3);
+        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5);
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.launches = 0;
         w.ensure_cfg(0);
-        if (!fgcr) w.ensure_cfg(ci);
+        if (!fgcr) w.ensure_cfg(normal ? 1 : ci);
         cudaStream_t s = lat->stream;
         const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
         const LaunchCfg& pl = w.cfg[0].per_lat[0];
@@ -1132,15 +1196,16 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol) {
             return fgcr ? w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter) : w.solve(ci, dag, rhs, sol, tol, maxiter);
         };
-        Workspace::Result rx = run(false, w.phi64, w.x64);
+        Workspace::Result rx, ry;
+        if (normal) w.solve_normal(w.phi64, tol, maxiter, rx, ry, /*check_y=*/true);
+        else rx = run(false, w.phi64, w.x64);
         double* dX = out_device(X, bytes, lat->stage_out);
         CK(ops_f64().unpack(pl, w.x64.ptr(), dX, s));
         w.launches += 1;
         finish_out(X, dX, bytes, s);
-        Workspace::Result ry;
         bool have_y = false;
         if (Y) {
-            ry = run(true, w.x64, w.y64);
+            if (!normal) ry = run(true, w.x64, w.y64);
             have_y = true;
             double* dY = out_device(Y, bytes, lat->stage_out);
             CK(ops_f64().unpack(pl, w.y64.ptr(), dY, s));
@@ -1240,12 +1305,12 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         const int ci = algo_index(algo);
-        const bool fgcr = (ci >= 3);
+        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5);
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.launches = 0;
         w.ensure_cfg(0);
-        if (!fgcr) w.ensure_cfg(ci);
+        if (!fgcr) w.ensure_cfg(normal ? 1 : ci);
         ensure_odd(w);
         cudaStream_t s = lat->stream;
         const KrylovOps& o = ops_f64();
@@ -1262,11 +1327,16 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
             w.launches += 1;
             return r;
         };
-        Workspace::Result rx = run(false, w.phi64, w.x64, w.xo64);
+        Workspace::Result rx, ry;
+        if (normal) {
+            w.solve_normal(w.phi64, tol, maxiter, rx, ry, /*check_y=*/false, &w.xo64, &w.yo64);
+        } else {
+            rx = run(false, w.phi64, w.x64, w.xo64);
+        }
         double* dX = out_device(X, bytes, lat->stage_out);
         CK(o.unpack(pl, w.x64.ptr(), dX, s));
         finish_out(X, dX, bytes, s);
-        Workspace::Result ry = run(true, w.x64, w.y64, w.yo64);
+        if (!normal) ry = run(true, w.x64, w.y64, w.yo64);
         double* dY = out_device(Y, bytes, lat->stage_out);
         CK(o.unpack(pl, w.y64.ptr(), dY, s));
         finish_out(Y, dY, bytes, s);
@@ -1338,11 +1408,12 @@ sf_status sf_batch_solve(sf_batch* b, sf_algo algo, const double* const* phi, do
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         Workspace& w = b->ws;
         const int ci = algo_index(algo);
-        REQUIRE(ci < 3, "batches run the BiCGStab algorithms");
+        REQUIRE(ci < 3 || ci == 5, "batches run the BiCGStab and CG algorithms");
+        const bool normal = (ci == 5);
         CK(cudaSetDevice(w.device));
         w.launches = 0;
         w.ensure_cfg(0);
-        w.ensure_cfg(ci);
+        w.ensure_cfg(normal ? 1 : ci);
         cudaStream_t s = w.stream;
         for (int l = 0; l < w.nlat; ++l) {
             REQUIRE(phi[l] != nullptr && X[l] != nullptr, "NULL array in batch");
@@ -1352,9 +1423,13 @@ sf_status sf_batch_solve(sf_batch* b, sf_algo algo, const double* const* phi, do
             if (d != phi[l]) CK(cudaStreamSynchronize(s));
             w.launches += 1;
         }
-        Workspace::Result rx = w.solve(ci, false, w.phi64, w.x64, tol, maxiter);
-        Workspace::Result ry;
-        if (Y) ry = w.solve(ci, true, w.x64, w.y64, tol, maxiter);
+        Workspace::Result rx, ry;
+        if (normal) {
+            w.solve_normal(w.phi64, tol, maxiter, rx, ry, /*check_y=*/true);
+        } else {
+            rx = w.solve(ci, false, w.phi64, w.x64, tol, maxiter);
+            if (Y) ry = w.solve(ci, true, w.x64, w.y64, tol, maxiter);
+        }
         for (int l = 0; l < w.nlat; ++l) {
             const size_t bytes = (size_t)w.nrhs * w.lats[l]->Vh * 24 * sizeof(double);
             double* dX = out_device(X[l], bytes, w.io);

@@ -412,6 +412,8 @@ enum FinMode {
     FIN_INIT = 3,  // inner-solve start from |b|^2
     FIN_NORM = 4,  // out[i] = sum
     FIN_DOT = 5,   // ((double2*) out)[i] = (re, im)
+    FIN_CG = 6,        // CG: rho' = |r|^2, beta = rho' / rho, convergence
+    FIN_INIT_CG = 7,   // CG start: rho = |b|^2, omega = 0 (the shared update kernels then do CG)
 };
 constexpr int FIN_THREADS = 512;
 
@@ -421,6 +423,7 @@ __device__ __forceinline__ void set_loop_cond(const SolverCtx& ctx, int nlat, in
     int any = 0;
     for (int i = 0; i < nlat * nrhs; ++i) any |= ctx.st[i].active;
     const int n = atomicAdd(ctx.loop_count, 1) + 1;
+    ctx.loop_count[3] += 1;  // iterations of the whole solve (launch accounting)
     const int go = (any && n < ctx.loop_count[1]) ? 1 : 0;
     ctx.loop_count[2] = go;  // read by the host when the loop runs without a graph
     if (ctx.use_cond) cudaGraphSetConditional(ctx.cond, (unsigned)go);
@@ -439,15 +442,16 @@ __device__ __forceinline__ void fin_apply(const SolverCtx& ctx, int i, int tid, 
         return;
     }
     KState& st = ctx.st[i];
-    if (MODE == FIN_INIT) {
+    if (MODE == FIN_INIT || MODE == FIN_INIT_CG) {
         const OState& o = ctx.ost[i];
+        const float om = (MODE == FIN_INIT_CG) ? 0.f : 1.f;
         st.rho = make_double2(sres[tid], 0.0);
         st.rr = sres[tid];
         st.alpha = make_double2(1.0, 0.0);
-        st.omega = make_double2(1.0, 0.0);
+        st.omega = make_double2((double)om, 0.0);
         st.beta = make_double2(0.0, 0.0);
         st.alpha_f = make_float2(1.f, 0.f);
-        st.omega_f = make_float2(1.f, 0.f);
+        st.omega_f = make_float2(om, 0.f);
         st.beta_f = make_float2(0.f, 0.f);
         st.iters = 0;
         st.maxiter = maxiter;
@@ -474,6 +478,20 @@ __device__ __forceinline__ void fin_apply(const SolverCtx& ctx, int i, int tid, 
             st.omega = make_double2(0.0, 0.0);
             st.omega_f = make_float2(0.f, 0.f);
         }
+    } else if (MODE == FIN_CG) {
+        const double rr = sres[3 * tid + 2];
+        st.rr = rr;
+        st.iters += 1;
+        const bool rho0 = (st.rho.x == 0.0);
+        if (!rho0) {
+            const double b = rr / st.rho.x;
+            st.beta = make_double2(b, 0.0);
+            st.beta_f = make_float2((float)b, 0.f);
+        }
+        st.rho = make_double2(rr, 0.0);
+        if (rho0) st.flags |= 1;
+        const bool go = (rr > st.target2) && (st.iters < st.maxiter) && !rho0;
+        st.active = go ? 1 : 0;
     } else if (MODE == FIN_XR) {
         const double2 rho_new = make_double2(sres[3 * tid], sres[3 * tid + 1]);
         const double rr = sres[3 * tid + 2];
@@ -521,7 +539,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict
         if (lane == 0) sres[r] = acc_to_double(a);
     }
     __syncthreads();
-    if (MODE == FIN_INIT && l == 0 && tid == 0) *ctx.loop_count = 0;
+    if ((MODE == FIN_INIT || MODE == FIN_INIT_CG) && l == 0 && tid == 0) *ctx.loop_count = 0;
     if (tid < nrhs) fin_apply<MODE, RV>(ctx, l * nrhs + tid, tid, sres, out, maxiter);
 }
 
@@ -1045,6 +1063,35 @@ struct OpsImpl {
     }
     static int iteration_kernels(const LaunchCfg&) { return 10; }
 
+    // ---- one CG iteration on A = Dhat Dhat^dag (Hermitian, positive) for every
+    // active rhs, with omega = 0 in the BiCGStab update kernels:
+    //   t = Dhat^dag p; q = Dhat t (in v), <p, q> -> alpha = rho / <p, q>;
+    //   s = r - alpha q; x += alpha p, r = s, |r|^2 -> beta = |r|^2 / rho;
+    //   p = r + beta p (sets the loop condition).  9 kernels.
+    static cudaError_t iterate_cg(const LaunchCfg& c, bool, const IterFields& f, const SolverCtx* ctx,
+                                  cudaStream_t st) {
+        const FieldPtr none{nullptr, nullptr};
+        const bool copy = !std::is_same<PV, PH>::value;
+        if (copy) return cudaErrorInvalidValue;  // CG runs with FP32 (or FP64) hop operands
+        cudaError_t e;
+        if ((e = hop(c, 1, true, f.p, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
+        if ((e = tail(c, 0, true, RED_NONE, f.tmp, f.p, none, f.t, none, 1.0, -1.0, 2, ctx, nullptr, st)) !=
+            cudaSuccess)
+            return e;
+        if ((e = hop(c, 1, false, f.t, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
+        if ((e = tail(c, 0, false, RED_R0V, f.tmp, f.t, none, f.v, f.p, 1.0, -1.0, 2, ctx, nullptr, st)) !=
+            cudaSuccess)
+            return e;
+        if ((e = s_update(c, f.r, f.v, f.s, f.sh, ctx, st)) != cudaSuccess) return e;
+        SF_NR_SWITCH(c.NR, {
+            launch_pdl(k_xr_update<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
+                       wf<PV>(f.x), wf<PV>(f.r), cf<PV>(f.p), cf<PV>(f.s), cf<PV>(f.t), cf<PV>(f.r0), *ctx);
+        });
+        launch_finish<3, typename AccOf<typename PV::real>::T, FIN_CG, typename PV::real>(c, *ctx, nullptr, 0, st);
+        return p_update(c, f.p, f.ph, f.r, f.v, ctx, st);
+    }
+    static int iteration_kernels_cg(const LaunchCfg&) { return 9; }
+
     static cudaError_t init(const LaunchCfg& c, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
                             FieldPtr ph, const SolverCtx* ctx, int maxiter, cudaStream_t st) {
         SF_NR_SWITCH(c.NR, {
@@ -1054,6 +1101,17 @@ struct OpsImpl {
         });
         launch_finish<1, typename AccOf<typename PV::real>::T, FIN_INIT, typename PV::real>(c, *ctx, nullptr, maxiter,
                                                                                            st);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t init_cg(const LaunchCfg& c, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
+                               FieldPtr ph, const SolverCtx* ctx, int maxiter, cudaStream_t st) {
+        SF_NR_SWITCH(c.NR, {
+            launch_pdl(k_inner_init<PV, PH, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
+                       cf<P64>(r64), wf<PV>(x), wf<PV>(r), wf<PV>(r0), wf<PV>(p), wf<PH>(ph), *ctx);
+        });
+        launch_finish<1, typename AccOf<typename PV::real>::T, FIN_INIT_CG, typename PV::real>(c, *ctx, nullptr,
+                                                                                              maxiter, st);
         return cudaGetLastError();
     }
 
@@ -1128,6 +1186,9 @@ struct OpsImpl {
         o.unpack_h = &unpack_h;
         o.iterate = &iterate;
         o.iteration_kernels = &iteration_kernels;
+        o.init_cg = &init_cg;
+        o.iterate_cg = &iterate_cg;
+        o.iteration_kernels_cg = &iteration_kernels_cg;
         return o;
     }
 };

@@ -55,7 +55,7 @@ struct SolverCtx {
     KState* st;           // [nlat * nrhs]
     OState* ost;          // [nlat * nrhs]
     double* partials;     // [3 * nrhs * nblocks] per-block partial sums (k_finish adds them)
-    int* loop_count;      // [0] iterations of the WHILE loop, [1] their cap, [2] continue flag
+    int* loop_count;      // [0] iterations of the WHILE loop, [1] their cap, [2] continue flag, [3] solve total
     cudaGraphConditionalHandle cond;
     int use_cond;
 };
@@ -104,6 +104,11 @@ struct KrylovOps {
     // number of kernels it launches
     cudaError_t (*iterate)(const LaunchCfg&, bool dag, const IterFields&, const SolverCtx*, cudaStream_t);
     int (*iteration_kernels)(const LaunchCfg&);
+    // CG on Dhat Dhat^dag (the normal-equation route): start and one iteration
+    cudaError_t (*init_cg)(const LaunchCfg&, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
+                           FieldPtr ph, const SolverCtx*, int maxiter, cudaStream_t);
+    cudaError_t (*iterate_cg)(const LaunchCfg&, bool dag, const IterFields&, const SolverCtx*, cudaStream_t);
+    int (*iteration_kernels_cg)(const LaunchCfg&);
 };
 
 // Launch a kernel of this library with programmatic stream serialization

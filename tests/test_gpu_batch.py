@@ -43,7 +43,7 @@ def _solve_batch(sf, lts, nrhs, algo, tol, check):
     return infos, X, Y
 
 
-@pytest.mark.parametrize("algo", ["mixed_dc", "bicgstab", "mixed_dc_half"])
+@pytest.mark.parametrize("algo", ["mixed_dc", "bicgstab", "mixed_dc_half", "cg_normal"])
 def test_small_uneven_batch(sf, algo):
     lts = [inputs.Lattice(4, 4, 0.3, 0.125, 101), inputs.Lattice(6, 5, 0.35, 0.13, 102),
            inputs.Lattice(8, 8, 0.25, 0.13, 103), inputs.Lattice(4, 7, 0.2, 0.12, 104)]

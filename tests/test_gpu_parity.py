@@ -143,7 +143,7 @@ def test_host_and_device_pointers_agree(sf):
     lat_h.close()
 
 
-@pytest.mark.parametrize("algo", ["bicgstab", "mixed_dc", "mixed_dc_half"])
+@pytest.mark.parametrize("algo", ["bicgstab", "mixed_dc", "mixed_dc_half", "cg_normal"])
 def test_solve_sf8_plain_config(sf, algo):
     """8^3x8 SF, eps 0.3, kappa 0.125, theta 0.5, 1 RHS, solved to 1e-12."""
     w = inputs.workload("sf8_plain_1rhs")
@@ -190,7 +190,7 @@ def test_solve_five_rhs_and_force_sf12(sf):
     lat.close()
 
 
-@pytest.mark.parametrize("algo", ["mixed_dc", "bicgstab", "fgcr"])
+@pytest.mark.parametrize("algo", ["mixed_dc", "bicgstab", "fgcr", "cg_normal"])
 def test_md_force_step_matches_separate_calls(sf, algo):
     """Alg. 2 in one call reuses the odd-site hops of the final residuals: the
     same X, Y and force, bitwise, as solve_block followed by fermion_force
