@@ -479,7 +479,7 @@ __device__ __forceinline__ void fin_apply(const SolverCtx& ctx, int i, int tid, 
             st.omega_f = make_float2(0.f, 0.f);
         }
     } else if (MODE == FIN_CG) {
-        const double rr = sres[3 * tid + 2];
+        const double rr = sres[tid];
         st.rr = rr;
         st.iters += 1;
         const bool rho0 = (st.rho.x == 0.0);
@@ -723,6 +723,54 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_s_update
             if (COPY) store_spinor<PH, RV>(sh, vbase<PH>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), a);
         }
     }
+}
+
+// CG: x += alpha p ; r -= alpha q ; |r|^2 (q = A p in v)
+template <typename PV, int NR>
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_cg_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                    Field<PV> x, Field<PV> r, CField<PV> p, CField<PV> q,
+                                                    SolverCtx ctx) {
+    pdl_enter();
+    using RV = typename PV::real;
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y * NR;
+    const int nval = min(NR, nrhs - r0);
+    using A = typename AccOf<RV>::T;
+    A red[NR][1];
+    bool act[NR];
+    cpx<RV> al[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        red[j][0] = acc_zero<A>();
+        act[j] = (j < nval) && ctx.st[l * nrhs + r0 + j].active;
+        if (act[j]) al[j] = Coef<RV>::alpha(ctx.st[l * nrhs + r0 + j]);
+    }
+    for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (!act[j]) continue;
+            const long long vb = vbase<PV>(g, r0 + j), sb = sbase(g, r0 + j);
+            cpx<RV> xa[4][3], ra[4][3], pa[4][3], qa[4][3];
+            load_spinor<PV, RV>(CField<PV>{x.v, x.scale}, vb, g.Vpad, cb, sb, xa);
+            load_spinor<PV, RV>(CField<PV>{r.v, r.scale}, vb, g.Vpad, cb, sb, ra);
+            load_spinor<PV, RV>(p, vb, g.Vpad, cb, sb, pa);
+            load_spinor<PV, RV>(q, vb, g.Vpad, cb, sb, qa);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    xa[sp][c] = xa[sp][c] + al[j] * pa[sp][c];
+                    ra[sp][c] = ra[sp][c] - al[j] * qa[sp][c];
+                }
+            store_spinor<PV, RV>(x, vb, g.Vpad, cb, sb, xa);
+            store_spinor<PV, RV>(r, vb, g.Vpad, cb, sb, ra);
+            norm_acc(ra, red[j][0]);
+        }
+    }
+    block_partials<NR, 1>(red, nrhs, ctx.partials);
 }
 
 // x += alpha p + omega s ; r = s - omega t ; rho' = <r0, r>, rr = |r|^2
@@ -1064,10 +1112,11 @@ struct OpsImpl {
     static int iteration_kernels(const LaunchCfg&) { return 10; }
 
     // ---- one CG iteration on A = Dhat Dhat^dag (Hermitian, positive) for every
-    // active rhs, with omega = 0 in the BiCGStab update kernels:
+    // active rhs:
     //   t = Dhat^dag p; q = Dhat t (in v), <p, q> -> alpha = rho / <p, q>;
-    //   s = r - alpha q; x += alpha p, r = s, |r|^2 -> beta = |r|^2 / rho;
-    //   p = r + beta p (sets the loop condition).  9 kernels.
+    //   x += alpha p, r -= alpha q, |r|^2 -> beta = |r|^2 / rho;
+    //   p = r + beta p (the BiCGStab p update with omega = 0; sets the loop
+    //   condition).  8 kernels.
     static cudaError_t iterate_cg(const LaunchCfg& c, bool, const IterFields& f, const SolverCtx* ctx,
                                   cudaStream_t st) {
         const FieldPtr none{nullptr, nullptr};
@@ -1082,15 +1131,14 @@ struct OpsImpl {
         if ((e = tail(c, 0, false, RED_R0V, f.tmp, f.t, none, f.v, f.p, 1.0, -1.0, 2, ctx, nullptr, st)) !=
             cudaSuccess)
             return e;
-        if ((e = s_update(c, f.r, f.v, f.s, f.sh, ctx, st)) != cudaSuccess) return e;
         SF_NR_SWITCH(c.NR, {
-            launch_pdl(k_xr_update<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
-                       wf<PV>(f.x), wf<PV>(f.r), cf<PV>(f.p), cf<PV>(f.s), cf<PV>(f.t), cf<PV>(f.r0), *ctx);
+            launch_pdl(k_cg_update<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
+                       wf<PV>(f.x), wf<PV>(f.r), cf<PV>(f.p), cf<PV>(f.v), *ctx);
         });
-        launch_finish<3, typename AccOf<typename PV::real>::T, FIN_CG, typename PV::real>(c, *ctx, nullptr, 0, st);
+        launch_finish<1, typename AccOf<typename PV::real>::T, FIN_CG, typename PV::real>(c, *ctx, nullptr, 0, st);
         return p_update(c, f.p, f.ph, f.r, f.v, ctx, st);
     }
-    static int iteration_kernels_cg(const LaunchCfg&) { return 9; }
+    static int iteration_kernels_cg(const LaunchCfg&) { return 8; }
 
     static cudaError_t init(const LaunchCfg& c, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
                             FieldPtr ph, const SolverCtx* ctx, int maxiter, cudaStream_t st) {
