@@ -197,6 +197,24 @@ struct sf_lattice {
 };
 
 // ---------------------------------------------------------------- workspace
+// Blocks of one lattice in a launch.  Tiles are numbered time-slice fastest
+// (column c of TS spatial sites, then x0), and block b owns the contiguous
+// tiles [b ntiles / nblk, (b + 1) ntiles / nblk).  With nblk a multiple of
+// the ncol columns, every block owns one segment of x0 slices of one column,
+// and all blocks of a wave step through the same slices together: a site's
+// x1 neighbours (another column) are read at the same step and its x0
+// neighbours (the next tiles of the same block) a step later, so they come
+// from L2 (at 32^4, 8 blocks per SM out of phase with the columns read each
+// input spinor about 2.1 times from DRAM; in phase, 1.2 times).  nseg
+// segments per column give about 12 blocks per SM (measured best at 16^4 to
+// 32^4 among 4, 8, 12); small lattices get one tile per block.
+inline int blocks_for(int L3h, int T, int TS, int sm_count) {
+    const int ncol = (L3h + TS - 1) / TS;
+    const int ntiles = ncol * (T - 1);
+    const int nseg = std::max(1, std::min(T - 1, (12 * sm_count) / ncol));
+    return std::min(ntiles, ncol * nseg);
+}
+
 // Tilings the kernels of a precision index (0 FP64, 1 FP32, 2 FP16 hop
 // operands, 3 FP64 vector kernels) are compiled for: blocks of TS sites x
 // ceil(nrhs / NR) right-hand-side groups within the kernels' launch bounds
@@ -284,11 +302,13 @@ struct Workspace {
         ost.ensure(n * sizeof(OState));
         CK(cudaMemset(st.p, 0, n * sizeof(KState)));
         CK(cudaMemset(ost.p, 0, n * sizeof(OState)));
-        // the most blocks any tiling can use: TS = 32
+        // the most blocks any tiling can use: the largest of TS = 32, 64, 128
         long long maxblk = 0;
         for (int l = 0; l < nlat; ++l) {
             const int L3h = ls[l]->L * ls[l]->L * ls[l]->L / 2;
-            maxblk += std::min(((L3h + 31) / 32) * (ls[l]->T - 1), 8 * sm_count);
+            int m = 0;
+            for (int TS : {32, 64, 128}) m = std::max(m, blocks_for(L3h, ls[l]->T, TS, sm_count));
+            maxblk += m;
         }
         // per-block partial sums of the reductions (3 rows per rhs at most)
         partials.ensure((size_t)3 * nrhs * maxblk * sizeof(double));
@@ -310,7 +330,7 @@ struct Workspace {
             LatDev g = lats[l]->base_desc();
             g.soff = soff[l];
             g.ntiles = ((g.L3h + TS - 1) / TS) * (g.T - 1);  // time-slice-fastest tiles
-            g.nblk = std::min(g.ntiles, 8 * sm_count);
+            g.nblk = blocks_for(g.L3h, g.T, TS, sm_count);
             g.blk0 = blk;
             blk += g.nblk;
             c.host[l] = g;

@@ -851,14 +851,21 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_p_update
             const cpx<RV> be = Coef<RV>::beta(k);
             const cpx<RV> om = Coef<RV>::omega(k);
             const long long vb = vbase<PV>(g, r0 + j), sb = sbase(g, r0 + j);
-            cpx<RV> pa[4][3], ra[4][3], va[4][3];
+            cpx<RV> pa[4][3], ra[4][3];
             load_spinor<PV, RV>(CField<PV>{p.v, p.scale}, vb, g.Vpad, cb, sb, pa);
             load_spinor<PV, RV>(r, vb, g.Vpad, cb, sb, ra);
-            load_spinor<PV, RV>(v, vb, g.Vpad, cb, sb, va);
+            if (om.re != (RV)0 || om.im != (RV)0) {  // BiCGStab; CG runs with omega = 0 and skips v
+                cpx<RV> va[4][3];
+                load_spinor<PV, RV>(v, vb, g.Vpad, cb, sb, va);
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) pa[sp][c] = pa[sp][c] - om * va[sp][c];
+            }
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) pa[sp][c] = ra[sp][c] + be * (pa[sp][c] - om * va[sp][c]);
+                for (int c = 0; c < 3; ++c) pa[sp][c] = ra[sp][c] + be * pa[sp][c];
             store_spinor<PV, RV>(p, vb, g.Vpad, cb, sb, pa);
             if (COPY) store_spinor<PH, RV>(ph, vbase<PH>(g, r0 + j), g.Vpad, cb, sb, pa);
         }
