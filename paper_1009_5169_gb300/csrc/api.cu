@@ -683,38 +683,48 @@ void Workspace::autotune(int ci) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int bTS = 64, bNR = 1, bpipe = 0;
-    const FieldPtr none{nullptr, nullptr};
+    // every admissible tiling, timed in three interleaved rounds; each keeps its
+    // fastest round (the launches are a few microseconds, so one round is noisy)
+    struct Cand {
+        int TS, NR, pipe;
+        float ms;
+    };
+    std::vector<Cand> cands;
     for (int pipe = 0; pipe <= 1; ++pipe)
         for (int NR : nrs_all) {
             if (NR > nrhs) continue;
-            for (int TS : tss) {
-                if (!tiling_ok(ci, TS, NR, nrhs, pipe)) continue;
-                set_tiling(ci, TS, NR, pipe);
-                const LaunchCfg& lc = cfg[ci].lc;
-                Inner& in = inner[ci];
-                auto run = [&]() {
-                    CK(o.hop(lc, 1, false, hop_in(ci, in.p, in.ph), in.tmp.ptr(), 1.0, 0, nullptr, stream));
-                    CK(o.tail(lc, 0, false, RED_NONE, in.tmp.ptr(), in.p.ptr(), none, in.v.ptr(), none, 1.0, -1.0,
-                              2, nullptr, nullptr, stream));
-                };
-                run();
-                run();
-                CK(cudaEventRecord(e0, stream));
-                const int reps = 12;
-                for (int r = 0; r < reps; ++r) run();
-                CK(cudaEventRecord(e1, stream));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) {
-                    best = ms;
-                    bTS = TS;
-                    bNR = NR;
-                    bpipe = pipe;
-                }
-            }
+            for (int TS : tss)
+                if (tiling_ok(ci, TS, NR, nrhs, pipe)) cands.push_back(Cand{TS, NR, pipe, 1e30f});
+        }
+    const FieldPtr none{nullptr, nullptr};
+    for (int round = 0; round < 3; ++round)
+        for (Cand& cd : cands) {
+            set_tiling(ci, cd.TS, cd.NR, cd.pipe);
+            const LaunchCfg& lc = cfg[ci].lc;
+            Inner& in = inner[ci];
+            auto run = [&]() {
+                CK(o.hop(lc, 1, false, hop_in(ci, in.p, in.ph), in.tmp.ptr(), 1.0, 0, nullptr, stream));
+                CK(o.tail(lc, 0, false, RED_NONE, in.tmp.ptr(), in.p.ptr(), none, in.v.ptr(), none, 1.0, -1.0, 2,
+                          nullptr, nullptr, stream));
+            };
+            run();
+            CK(cudaEventRecord(e0, stream));
+            const int reps = 8;
+            for (int r = 0; r < reps; ++r) run();
+            CK(cudaEventRecord(e1, stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            cd.ms = std::min(cd.ms, ms);
+        }
+    int bTS = 64, bNR = 1, bpipe = 0;
+    float best = 1e30f;
+    for (const Cand& cd : cands)
+        if (cd.ms < best) {
+            best = cd.ms;
+            bTS = cd.TS;
+            bNR = cd.NR;
+            bpipe = cd.pipe;
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
