@@ -352,24 +352,25 @@ def run_ours(args, rank, world, local_rank):
         bX = [torch.empty_like(p) for p in bphi]
         bY = [torch.empty_like(p) for p in bphi]
         batch = sf.Batch(blats, wb.nrhs)
-        batch.solve("mixed_dc", bphi, bX, bY, tol=wb.tol, maxiter=args.maxiter)
+        balgo = args.algo if args.algo in ("bicgstab", "mixed_dc", "mixed_dc_half", "cg_normal") else "mixed_dc"
+        batch.solve(balgo, bphi, bX, bY, tol=wb.tol, maxiter=args.maxiter)
         torch.cuda.synchronize()
         reps = 3
         t0 = time.perf_counter()
         for _ in range(reps):
-            binfo = batch.solve("mixed_dc", bphi, bX, bY, tol=wb.tol, maxiter=args.maxiter)
+            binfo = batch.solve(balgo, bphi, bX, bY, tol=wb.tol, maxiter=args.maxiter)
         torch.cuda.synchronize()
         tb = (time.perf_counter() - t0) / reps
         for l, bl in enumerate(blats):
-            sf.solve_block(bl, "mixed_dc", bphi[l], bX[l], bY[l], tol=wb.tol, maxiter=args.maxiter)
+            sf.solve_block(bl, balgo, bphi[l], bX[l], bY[l], tol=wb.tol, maxiter=args.maxiter)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for l, bl in enumerate(blats):
-            sf.solve_block(bl, "mixed_dc", bphi[l], bX[l], bY[l], tol=wb.tol, maxiter=args.maxiter)
+            sf.solve_block(bl, balgo, bphi[l], bX[l], bY[l], tol=wb.tol, maxiter=args.maxiter)
         torch.cuda.synchronize()
         ts = time.perf_counter() - t0
         batched = {"workload": "24 SF fields: 8 each of 8^4, 12^4, 16^4; eps 0.15/0.25/0.35; kappa 0.13; 5 RHS; "
-                               "X and Y to 1e-10, FP32 inner / FP64 outer",
+                               "X and Y to 1e-10, FP32 inner / FP64 outer", "algo": balgo,
                    "batched_solves_per_s": round(len(blats) / tb, 2), "batch_ms": round(tb * 1e3, 2),
                    "one_lattice_at_a_time_ms": round(ts * 1e3, 2), "speedup": round(ts / tb, 2),
                    "max_true_rel_resid": max(max(max(i["true_resid"]), max(i["true_resid_y"])) for i in binfo)}
@@ -528,8 +529,8 @@ def learned_section(args, dev, local_rank, stream):
         sf.set_preconditioner(lat, net)
         phi = torch.from_numpy(inputs.sources(lt.L, lt.T, w.nrhs, inputs.SEED_BASE + 1000 + h)).to(dev)
         X, Y = torch.empty_like(phi), torch.empty_like(phi)
-        for algo in ("fgcr_cnn", "fgcr", "bicgstab", "mixed_dc"):
-            if algo == "mixed_dc":   # the others run long enough that one-time set-up is negligible
+        for algo in ("fgcr_cnn", "fgcr", "bicgstab", "mixed_dc", "cg_normal"):
+            if algo in ("mixed_dc", "cg_normal"):   # the others run long enough that one-time set-up is negligible
                 sf.solve_block(lat, algo, phi, X, Y, tol=w.tol, maxiter=args.maxiter)
             torch.cuda.synchronize()
             a = time.perf_counter()
