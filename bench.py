@@ -54,7 +54,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("krylov_impl.cuh", "sf_device.cuh"):
+    for f in ("hop.cuh", "sf_device.cuh"):
         with open(os.path.join(ROOT, "paper_1009_5169_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

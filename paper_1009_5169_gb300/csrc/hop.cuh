@@ -1,0 +1,307 @@
+// hop.cuh -- the Wilson hop H_oe / H_eo of the even/odd operator (Sec. 3.1,
+// Eq. 2 with the SF boundaries of Sec. 4) on the SoA field storage, for NR
+// right-hand sides per thread, plain or with the next directions' operands
+// fetched ahead, and the k_hop kernel that applies it to a whole block of
+// lattices.  The fused Dhat tail and the solver kernels build on it
+// (krylov_impl.cuh).
+//   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) lambda_mu psi(x+mu)
+//              + (1 + gamma_mu) U_mu(x-mu)^dag lambda_mu^* psi(x-mu),
+//   lambda_0 = 1, lambda_k = e^{i theta/L} (stored inside the spatial links);
+//   time hops leaving x0 = 1..T-1 are dropped (Dirichlet).
+#pragma once
+#include <type_traits>
+
+#include "sf_kernels.h"
+
+namespace sf {
+
+template <typename P> __host__ __device__ __forceinline__ CField<P> cf(FieldPtr f) {
+    return CField<P>{reinterpret_cast<const typename P::vec*>(f.v), f.s};
+}
+template <typename P> __host__ __device__ __forceinline__ Field<P> wf(FieldPtr f) {
+    return Field<P>{reinterpret_cast<typename P::vec*>(f.v), f.s};
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// element offsets of (lattice block, rhs)
+template <typename P>
+__device__ __forceinline__ long long vbase(const LatDev& g, int rhs) {
+    return (g.soff + (long long)rhs * g.Vpad) * P::NC;
+}
+__device__ __forceinline__ long long sbase(const LatDev& g, int rhs) { return g.soff + (long long)rhs * g.Vpad; }
+
+// Threads per block a kernel of a (precision, NR) configuration may be
+// launched with; it sets the register budget 65536 / MAXT per thread.
+// FP32/FP16 with NR = 1 is held to 96 registers (two 320-thread blocks per
+// SM): the hop is latency-bound and gains more from resident warps than from
+// the extra load hoisting a larger budget buys.
+template <typename P, int NR>
+struct KB {
+    static constexpr bool F64 = std::is_same<P, P64>::value;
+    static constexpr int MAXT = F64 ? (NR == 1 ? 256 : 128) : (NR == 1 ? 320 : NR == 2 ? 384 : 256);
+    static constexpr int MINB = F64 ? 1 : (NR == 1 ? 2 : 1);
+};
+// hop and tail kernels: the pipelined hop's blocks hold at most 256 threads
+// (up to 255 registers each for the operand buffers)
+template <typename P, int NR, bool PIPE>
+struct KBH {
+    static constexpr int MAXT = PIPE ? 256 : KB<P, NR>::MAXT;
+    static constexpr int MINB = PIPE ? 1 : KB<P, NR>::MINB;
+};
+
+// ------------------------------------------------------------ hop
+template <int MU, typename P, int NR, bool DAG>
+__device__ __forceinline__ void hop_dir(const LatDev& g, const SiteX& s, int cb, int out_par,
+                                        const CField<P>& in, int r0, int nval,
+                                        cpx<typename P::real> (&acc)[NR][4][3]) {
+    using R = typename P::real;
+    constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma_mu
+    constexpr int SB = -SF;
+    if (MU != 0 || s.x0 < g.T - 1) {
+        const int ncb = neighbour_cb<MU, +1>(g, s);
+        Link<R> U;
+        LinkLoad<P>::template load<MU>(g, out_par, cb, U);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j < nval) {
+                cpx<R> p[4][3];
+                load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
+                cpx<R> h[2][3], w[2][3];
+                project<MU, SF>(p, h);
+                mul_link(U, h, w);
+                expand_add<MU, SF>(acc[j], w);
+            }
+        }
+    }
+    if (MU != 0 || s.x0 > 1) {
+        const int ncb = neighbour_cb<MU, -1>(g, s);
+        Link<R> U;
+        LinkLoad<P>::template load<MU>(g, out_par ^ 1, ncb, U);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j < nval) {
+                cpx<R> p[4][3];
+                load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
+                cpx<R> h[2][3], w[2][3];
+                project<MU, SB>(p, h);
+                mul_link_dag(U, h, w);
+                expand_add<MU, SB>(acc[j], w);
+            }
+        }
+    }
+}
+
+template <typename P, int NR, bool DAG>
+__device__ __forceinline__ void hop_site(const LatDev& g, const SiteX& s, int cb, int out_par,
+                                         const CField<P>& in, int r0, int nval,
+                                         cpx<typename P::real> (&acc)[NR][4][3]) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[j][sp][a] = cpx<typename P::real>{0, 0};
+    hop_dir<0, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    hop_dir<1, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    hop_dir<2, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    hop_dir<3, P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+}
+
+// ------------------------------------------------------------ pipelined hop
+// FP32 / FP16 operands with NR <= 2: the raw operands of hop H (H = 2 mu,
+// + 1 for the backward hop) are loaded PF hops ahead of their use, so a
+// site's eight dependent load round trips overlap about PF at a time.  This
+// pays in registers (PF buffers) what it saves in latency: for small
+// lattices, whose launches hold a few warps per SM; the autotuner chooses.
+template <typename P, int NR> struct HopBuf;
+template <int NR> struct HopBuf<P32, NR> {
+    float4 u[3];       // link rows 0, 1
+    float4 s[NR][6];   // neighbour spinors
+};
+template <int NR> struct HopBuf<P16, NR> {
+    uint2 u[3];
+    uint4 s[NR][3];
+    float sc[NR];
+};
+template <int NR> struct PipeDepth { static constexpr int PF = (NR == 1) ? 4 : 2; };
+
+template <int H, typename P, int NR>
+__device__ __forceinline__ void hop_fetch(const LatDev& g, const SiteX& s, int cb, int out_par, const CField<P>& in,
+                                          int r0, int nval, HopBuf<P, NR>& b, bool& valid) {
+    constexpr int MU = H >> 1;
+    constexpr bool FWD = (H & 1) == 0;
+    valid = (MU != 0) || (FWD ? (s.x0 < g.T - 1) : (s.x0 > 1));
+    if (!valid) return;
+    const int ncb = neighbour_cb<MU, FWD ? +1 : -1>(g, s);
+    const int lpar = FWD ? out_par : (out_par ^ 1);
+    const int lcb = FWD ? cb : ncb;
+    if constexpr (std::is_same<P, P32>::value) {
+        const float4* ub = g.u32 + ((long long)(MU * 2 + lpar) * 3) * g.Vpad + lcb;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b.u[k] = __ldg(ub + (long long)k * g.Vpad);
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if (j < nval) {
+                const float4* sp = in.v + vbase<P32>(g, r0 + j) + ncb;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) b.s[j][k] = __ldg(sp + (long long)k * g.Vpad);
+            }
+    } else {
+        const uint2* ub = g.u16 + ((long long)(MU * 2 + lpar) * 3) * g.Vpad + lcb;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b.u[k] = __ldg(ub + (long long)k * g.Vpad);
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if (j < nval) {
+                const uint4* sp = in.v + vbase<P16>(g, r0 + j) + ncb;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) b.s[j][k] = __ldg(sp + (long long)k * g.Vpad);
+                b.sc[j] = __ldg(in.scale + sbase(g, r0 + j) + ncb);
+            }
+    }
+}
+
+template <int H, typename P, int NR, bool DAG>
+__device__ __forceinline__ void hop_apply(const LatDev& g, const HopBuf<P, NR>& b, bool valid, int nval,
+                                          cpx<float> (&acc)[NR][4][3]) {
+    constexpr int MU = H >> 1;
+    constexpr bool FWD = (H & 1) == 0;
+    constexpr int S = (FWD == DAG) ? +1 : -1;  // projector 1 + S gamma_mu
+    if (!valid) return;
+    Link<float> U;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float2 a, c;
+        if constexpr (std::is_same<P, P32>::value) {
+            a = make_float2(b.u[k].x, b.u[k].y);
+            c = make_float2(b.u[k].z, b.u[k].w);
+        } else {
+            a = h2f(b.u[k].x);
+            c = h2f(b.u[k].y);
+        }
+        U.m[(2 * k) / 3][(2 * k) % 3] = cpx<float>{a.x, a.y};
+        U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = cpx<float>{c.x, c.y};
+    }
+    rebuild_row2<MU>(g, U);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        if (j < nval) {
+            cpx<float> p[4][3];
+            if constexpr (std::is_same<P, P32>::value) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    p[(2 * k) / 3][(2 * k) % 3] = cpx<float>{b.s[j][k].x, b.s[j][k].y};
+                    p[(2 * k + 1) / 3][(2 * k + 1) % 3] = cpx<float>{b.s[j][k].z, b.s[j][k].w};
+                }
+            } else {
+                const float sc = b.sc[j];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float2 a = h2f(b.s[j][k].x), c = h2f(b.s[j][k].y), d = h2f(b.s[j][k].z),
+                                 e = h2f(b.s[j][k].w);
+                    p[(4 * k) / 3][(4 * k) % 3] = cpx<float>{a.x * sc, a.y * sc};
+                    p[(4 * k + 1) / 3][(4 * k + 1) % 3] = cpx<float>{c.x * sc, c.y * sc};
+                    p[(4 * k + 2) / 3][(4 * k + 2) % 3] = cpx<float>{d.x * sc, d.y * sc};
+                    p[(4 * k + 3) / 3][(4 * k + 3) % 3] = cpx<float>{e.x * sc, e.y * sc};
+                }
+            }
+            cpx<float> h[2][3], w[2][3];
+            project<MU, S>(p, h);
+            if (FWD) mul_link(U, h, w);
+            else mul_link_dag(U, h, w);
+            expand_add<MU, S>(acc[j], w);
+        }
+    }
+}
+
+// apply hop H from its buffer, then reuse the buffer for hop H + PF
+template <int H, typename P, int NR, bool DAG, int PF>
+__device__ __forceinline__ void hop_step(const LatDev& g, const SiteX& s, int cb, int out_par, const CField<P>& in,
+                                         int r0, int nval, HopBuf<P, NR> (&b)[PF], bool (&v)[8],
+                                         cpx<float> (&acc)[NR][4][3]) {
+    hop_apply<H, P, NR, DAG>(g, b[H % PF], v[H], nval, acc);
+    if constexpr (H + PF < 8) hop_fetch<H + PF, P, NR>(g, s, cb, out_par, in, r0, nval, b[H % PF], v[H + PF]);
+}
+
+template <typename P, int NR, bool DAG>
+__device__ __forceinline__ void hop_site_pipe(const LatDev& g, const SiteX& s, int cb, int out_par,
+                                              const CField<P>& in, int r0, int nval, cpx<float> (&acc)[NR][4][3]) {
+    constexpr int PF = PipeDepth<NR>::PF;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[j][sp][a] = cpx<float>{0.f, 0.f};
+    HopBuf<P, NR> b[PF];
+    bool v[8];
+    hop_fetch<0, P, NR>(g, s, cb, out_par, in, r0, nval, b[0], v[0]);
+    hop_fetch<1, P, NR>(g, s, cb, out_par, in, r0, nval, b[1 % PF], v[1]);
+    if constexpr (PF > 2) hop_fetch<2, P, NR>(g, s, cb, out_par, in, r0, nval, b[2 % PF], v[2]);
+    if constexpr (PF > 3) hop_fetch<3, P, NR>(g, s, cb, out_par, in, r0, nval, b[3 % PF], v[3]);
+    hop_step<0, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<1, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<2, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<3, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<4, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<5, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<6, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+    hop_step<7, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
+}
+
+// the hop of one site for NR right-hand sides, plain or pipelined
+template <typename P, int NR, bool DAG, bool PIPE>
+__device__ __forceinline__ void hop_any(const LatDev& g, const SiteX& s, int cb, int out_par, const CField<P>& in,
+                                        int r0, int nval, cpx<typename P::real> (&acc)[NR][4][3]) {
+    if constexpr (PIPE) hop_site_pipe<P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    else hop_site<P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+}
+
+__device__ __forceinline__ bool rhs_active(const KState* st, int idx) { return st == nullptr || st[idx].active != 0; }
+
+
+// ------------------------------------------------------------ kernels
+// out(out_par) = coef * H in
+template <typename PI, typename PO, int NR, bool DAG, bool PIPE>
+__global__ void __launch_bounds__(KBH<PI, NR, PIPE>::MAXT, KBH<PI, NR, PIPE>::MINB) k_hop(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
+                                              CField<PI> in, Field<PO> out, double coef, int kpow,
+                                              const KState* __restrict__ st) {
+    pdl_enter();
+    using R = typename PI::real;
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int r0 = threadIdx.y * NR;
+    const int nval = min(NR, nrhs - r0);
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+        if (j < nval && rhs_active(st, l * nrhs + r0 + j)) any = true;
+    if (!any) return;
+    const R c = (R)(coef * (kpow == 0 ? 1.0 : kpow == 1 ? g.kappa : g.kappa * g.kappa));
+    for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
+        const SiteX s = decode_site(g, cb, out_par);
+        cpx<R> acc[NR][4][3];
+        hop_any<PI, NR, DAG, PIPE>(g, s, cb, out_par, in, r0, nval, acc);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j < nval) {
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) acc[j][sp][a] = c * acc[j][sp][a];
+                store_spinor<PO, R>(out, vbase<PO>(g, r0 + j), g.Vpad, cb, sbase(g, r0 + j), acc[j]);
+            }
+        }
+    }
+}
+
+}  // namespace sf
