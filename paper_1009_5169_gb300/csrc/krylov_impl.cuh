@@ -159,8 +159,7 @@ enum FinMode {
     FIN_INIT = 3,  // inner-solve start from |b|^2
     FIN_NORM = 4,  // out[i] = sum
     FIN_DOT = 5,   // ((double2*) out)[i] = (re, im)
-    FIN_CG = 6,        // CG: rho' = |r|^2, beta = rho' / rho, convergence
-    FIN_INIT_CG = 7,   // CG start: rho = |b|^2, omega = 0 (the shared update kernels then do CG)
+    FIN_INIT_CG = 7,   // CG start: gamma = |b|^2, iters = 0 (k_cg_step's first step), active, target2
 };
 constexpr int FIN_THREADS = 512;
 
@@ -225,20 +224,6 @@ __device__ __forceinline__ void fin_apply(const SolverCtx& ctx, int i, int tid, 
             st.omega = make_double2(0.0, 0.0);
             st.omega_f = make_float2(0.f, 0.f);
         }
-    } else if (MODE == FIN_CG) {
-        const double rr = sres[tid];
-        st.rr = rr;
-        st.iters += 1;
-        const bool rho0 = (st.rho.x == 0.0);
-        if (!rho0) {
-            const double b = rr / st.rho.x;
-            st.beta = make_double2(b, 0.0);
-            st.beta_f = make_float2((float)b, 0.f);
-        }
-        st.rho = make_double2(rr, 0.0);
-        if (rho0) st.flags |= 1;
-        const bool go = (rr > st.target2) && (st.iters < st.maxiter) && !rho0;
-        st.active = go ? 1 : 0;
     } else if (MODE == FIN_XR) {
         const double2 rho_new = make_double2(sres[3 * tid], sres[3 * tid + 1]);
         const double rr = sres[3 * tid + 2];
@@ -255,19 +240,17 @@ __device__ __forceinline__ void fin_apply(const SolverCtx& ctx, int i, int tid, 
     }
 }
 
-// Sum the block partials of each lattice (block l of this launch: rows
-// rhs * NQ + q over the lattice's blocks blk0 .. blk0 + nblk - 1, lane k
-// taking blocks k, k + 32, ... in batches of 16 independent loads, then a
-// shuffle tree: a fixed order) and apply MODE for each rhs.
-template <int NQ, typename A, int MODE, typename RV>
-__global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict__ lats, int nrhs, int nblocks,
-                                                         SolverCtx ctx, double* __restrict__ out, int maxiter) {
-    pdl_enter();
-    __shared__ double sres[MAX_RHS * 3];
-    const int l = blockIdx.x;
-    const int blk0 = lats[l].blk0, nblk = lats[l].nblk;
-    const A* __restrict__ partials = reinterpret_cast<const A*>(ctx.partials);
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = (int)blockDim.x >> 5;
+// The lattice sums of NQ quantities per rhs from the per-block partials: row
+// rhs * NQ + q over the lattice's blocks blk0 .. blk0 + nblk - 1.  Warp w of
+// nw takes rows w, w + nw, ...; lane k adds blocks k, k + 32, ... in batches
+// of 16 independent loads, then a shuffle tree.  The order depends on nw and
+// nblk only, so every block of a launch that calls it forms bitwise the same
+// sums.  Writes sres[rhs * NQ + q]; the caller synchronises before reading.
+template <int NQ, typename A>
+__device__ __forceinline__ void lattice_sums(const double* __restrict__ partials_, int nrhs, int nblocks, int blk0,
+                                             int nblk, int tid, int nthreads, double* sres) {
+    const A* __restrict__ partials = reinterpret_cast<const A*>(partials_);
+    const int lane = tid & 31, w = tid >> 5, nw = nthreads >> 5;
     for (int r = w; r < nrhs * NQ; r += nw) {
         const A* src = partials + (long long)r * nblocks + blk0;
         A a = acc_zero<A>();
@@ -285,12 +268,22 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict
         for (int off = 16; off > 0; off >>= 1) a = acc_add(a, acc_shfl_down(a, off));
         if (lane == 0) sres[r] = acc_to_double(a);
     }
+}
+
+// Sum the block partials of each lattice (block l of this launch) and apply
+// MODE for each rhs.
+template <int NQ, typename A, int MODE, typename RV>
+__global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict__ lats, int nrhs, int nblocks,
+                                                         SolverCtx ctx, double* __restrict__ out, int maxiter) {
+    pdl_enter();
+    __shared__ double sres[MAX_RHS * 3];
+    const int l = blockIdx.x;
+    const int tid = threadIdx.x;
+    lattice_sums<NQ, A>(ctx.partials, nrhs, nblocks, lats[l].blk0, lats[l].nblk, tid, (int)blockDim.x, sres);
     __syncthreads();
     if ((MODE == FIN_INIT || MODE == FIN_INIT_CG) && l == 0 && tid == 0) *ctx.loop_count = 0;
     if (tid < nrhs) fin_apply<MODE, RV>(ctx, l * nrhs + tid, tid, sres, out, maxiter);
 }
-
-
 
 template <int NQ, typename A, int MODE, typename RV>
 inline void launch_finish(const LaunchCfg& c, const SolverCtx& ctx, double* out, int maxiter, cudaStream_t st) {
@@ -327,7 +320,11 @@ __device__ __forceinline__ void norm_acc(const cpx<R> (&a)[4][3], A& n) {
 }
 
 // ------------------------------------------------------------ kernels
-// out(out_par) = a * xv + coef * H hin (+ zv) with a fused reduction
+// out(out_par) = a * xv + coef * H hin (+ zv) with a fused reduction.
+// RED_CG also opens a CG step: block 0 copies each rhs's state into the
+// *_prev fields and sets the loop condition from the active flags the
+// previous step left (the loop runs one pass with every rhs idle after the
+// last one stops).
 template <typename PH, typename PV, int NR, bool DAG, int RED, bool HASZ, bool PIPE>
 __global__ void __launch_bounds__(KBH<PH, NR, PIPE>::MAXT, KBH<PH, NR, PIPE>::MINB) k_tail(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
                                                CField<PH> hin, CField<PV> xv, CField<PV> zv, Field<PV> out,
@@ -336,7 +333,7 @@ __global__ void __launch_bounds__(KBH<PH, NR, PIPE>::MAXT, KBH<PH, NR, PIPE>::MI
     pdl_enter();
     using RH = typename PH::real;
     using RV = typename PV::real;
-    constexpr int NQ = (RED == RED_TS) ? 3 : (RED == RED_R0V) ? 2 : 1;
+    constexpr int NQ = (RED == RED_TS) ? 3 : (RED == RED_R0V || RED == RED_CG) ? 2 : 1;
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
     const int r0 = threadIdx.y * NR;
@@ -392,11 +389,26 @@ __global__ void __launch_bounds__(KBH<PH, NR, PIPE>::MAXT, KBH<PH, NR, PIPE>::MI
                     norm_acc(o, red[j][NQ > 2 ? 2 : 0]);
                 } else if (RED == RED_NORM) {
                     norm_acc(o, red[j][0]);
+                } else if (RED == RED_CG) {
+                    norm_acc(x, red[j][0]);
+                    norm_acc(o, red[j][NQ > 1 ? 1 : 0]);
                 }
             }
         }
     }
     if (RED == RED_NONE) return;
+    if (RED == RED_CG && blockIdx.x == 0) {
+        // start of a CG step (k_cg_step reads these copies while it writes the state)
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+        for (int i = tid; i < nlat * nrhs; i += nt) {
+            KState& k = ctx.st[i];
+            k.gamma_prev = k.rho.x;
+            k.alpha_prev = k.alpha.x;
+            k.active_prev = k.active;
+            k.iters_prev = k.iters;
+        }
+        if (tid == 0) set_loop_cond(ctx, nlat, nrhs);
+    }
     block_partials<NR, NQ>(red, nrhs, ctx.partials);
 }
 
@@ -434,52 +446,131 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_s_update
     }
 }
 
-// CG: x += alpha p ; r -= alpha q ; |r|^2 (q = A p in v)
+// One CG step on A = Dhat Dhat^dag in the single-reduction form of
+// Chronopoulos and Gear (1989): both inner products of a step come from one
+// pass.  From the lattice sums gamma = |r|^2 and delta = <r, A r> =
+// |Dhat^dag r|^2 of the partials the RED_CG tail wrote for this r (w = A r),
+//   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev)
+//   (beta = 0 and alpha = gamma / delta at the first step),
+//   p = r + beta p,  s = w + beta s  (s = A p),  x += alpha p,  r -= alpha s.
+// A rhs stops, before its update, when gamma <= target2, on breakdown
+// (gamma or the denominator not positive), and after maxiter steps.  Every
+// block sums its lattice's partials itself in a fixed order, so all blocks
+// take the same decisions; the lattice's first block records the step in
+// KState.  What the step reads of KState (*_prev, target2, maxiter) no block
+// of this launch writes.  alpha and beta are formed in double (the
+// denominator is a difference) and applied in the vector precision.
 template <typename PV, int NR>
-__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_cg_update(const LatDev* __restrict__ lats, int nlat, int nrhs,
-                                                    Field<PV> x, Field<PV> r, CField<PV> p, CField<PV> q,
-                                                    SolverCtx ctx) {
+__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_cg_step(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                  Field<PV> x, Field<PV> r, Field<PV> p, Field<PV> s,
+                                                  CField<PV> w, SolverCtx ctx) {
     pdl_enter();
     using RV = typename PV::real;
+    using A = typename AccOf<RV>::T;
+    __shared__ double sres[MAX_RHS * 2];
+    __shared__ RV scoef[MAX_RHS][2];
+    __shared__ int smode[MAX_RHS];
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    lattice_sums<2, A>(ctx.partials, nrhs, (int)gridDim.x, g.blk0, g.nblk, tid, (int)(blockDim.x * blockDim.y), sres);
+    __syncthreads();
+    if (tid < nrhs) {
+        KState& k = ctx.st[l * nrhs + tid];
+        const double gam = sres[2 * tid], del = sres[2 * tid + 1];
+        int mode = 0;  // 0: no update, 1: first step, 2: later step
+        int fl = 0;
+        double al = 0.0, be = 0.0;
+        const bool act = k.active_prev != 0;
+        if (act && gam > k.target2) {
+            const bool first = (k.iters_prev == 0);
+            be = first ? 0.0 : gam / k.gamma_prev;
+            const double den = first ? del : del - be * gam / k.alpha_prev;
+            if (gam > 0.0 && den > 0.0 && isfinite(gam / den)) {
+                al = gam / den;
+                mode = first ? 1 : 2;
+            } else {
+                fl = 1;
+            }
+        }
+        const RV alr = (RV)al, ber = (RV)be;
+        scoef[tid][0] = alr;
+        scoef[tid][1] = ber;
+        smode[tid] = mode;
+        if (act && blockIdx.x == g.blk0) {
+            k.rr = gam;
+            if (mode) {
+                k.rho = make_double2(gam, 0.0);
+                k.alpha = make_double2((double)alr, 0.0);
+                k.beta = make_double2((double)ber, 0.0);
+                k.iters = k.iters_prev + 1;
+                k.active = (k.iters < k.maxiter) ? 1 : 0;
+            } else {
+                k.active = 0;
+                k.flags |= fl;
+            }
+        }
+    }
+    __syncthreads();
     const int r0 = threadIdx.y * NR;
     const int nval = min(NR, nrhs - r0);
-    using A = typename AccOf<RV>::T;
-    A red[NR][1];
-    bool act[NR];
-    cpx<RV> al[NR];
+    int md[NR];
+    RV al[NR], be[NR];
+    bool any = false;
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-        red[j][0] = acc_zero<A>();
-        act[j] = (j < nval) && ctx.st[l * nrhs + r0 + j].active;
-        if (act[j]) al[j] = Coef<RV>::alpha(ctx.st[l * nrhs + r0 + j]);
+        md[j] = (j < nval) ? smode[r0 + j] : 0;
+        al[j] = (j < nval) ? scoef[r0 + j][0] : (RV)0;
+        be[j] = (j < nval) ? scoef[r0 + j][1] : (RV)0;
+        any = any || md[j] != 0;
     }
+    if (!any) return;
     for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
         const int cb = tile_cb(g, tile, threadIdx.x);
         if (cb < 0) continue;
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
-            if (!act[j]) continue;
+            if (!md[j]) continue;
             const long long vb = vbase<PV>(g, r0 + j), sb = sbase(g, r0 + j);
-            cpx<RV> xa[4][3], ra[4][3], pa[4][3], qa[4][3];
-            load_spinor<PV, RV>(CField<PV>{x.v, x.scale}, vb, g.Vpad, cb, sb, xa);
+            const bool later = (md[j] == 2);
+            // in three stages (p; x; s and r) to bound the live registers
+            cpx<RV> ra[4][3], ta[4][3], ua[4][3];
             load_spinor<PV, RV>(CField<PV>{r.v, r.scale}, vb, g.Vpad, cb, sb, ra);
-            load_spinor<PV, RV>(p, vb, g.Vpad, cb, sb, pa);
-            load_spinor<PV, RV>(q, vb, g.Vpad, cb, sb, qa);
+            if (later) {
+                load_spinor<PV, RV>(CField<PV>{p.v, p.scale}, vb, g.Vpad, cb, sb, ta);
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ta[sp][c] = ra[sp][c] + be[j] * ta[sp][c];
+            } else {
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ta[sp][c] = ra[sp][c];
+            }
+            store_spinor<PV, RV>(p, vb, g.Vpad, cb, sb, ta);
+            load_spinor<PV, RV>(CField<PV>{x.v, x.scale}, vb, g.Vpad, cb, sb, ua);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    xa[sp][c] = xa[sp][c] + al[j] * pa[sp][c];
-                    ra[sp][c] = ra[sp][c] - al[j] * qa[sp][c];
-                }
-            store_spinor<PV, RV>(x, vb, g.Vpad, cb, sb, xa);
+                for (int c = 0; c < 3; ++c) ua[sp][c] = ua[sp][c] + al[j] * ta[sp][c];
+            store_spinor<PV, RV>(x, vb, g.Vpad, cb, sb, ua);
+            load_spinor<PV, RV>(w, vb, g.Vpad, cb, sb, ta);
+            if (later) {
+                load_spinor<PV, RV>(CField<PV>{s.v, s.scale}, vb, g.Vpad, cb, sb, ua);
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ta[sp][c] = ta[sp][c] + be[j] * ua[sp][c];
+            }
+            store_spinor<PV, RV>(s, vb, g.Vpad, cb, sb, ta);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ra[sp][c] = ra[sp][c] - al[j] * ta[sp][c];
             store_spinor<PV, RV>(r, vb, g.Vpad, cb, sb, ra);
-            norm_acc(ra, red[j][0]);
         }
     }
-    block_partials<NR, 1>(red, nrhs, ctx.partials);
 }
 
 // x += alpha p + omega s ; r = s - omega t ; rho' = <r0, r>, rr = |r|^2
@@ -782,6 +873,9 @@ struct OpsImpl {
                 if (hz) SF_TAIL(RED_NORM, true); else SF_TAIL(RED_NORM, false);
                 launch_finish<1, A, FIN_NORM, RV>(c, k, norm_out, 0, st);
                 break;
+            case RED_CG:  // only Dhat^dag on the vector precision (tail() checks)
+                if constexpr (DAG && std::is_same<PV, PH>::value) SF_TAIL(RED_CG, false);
+                break;
         }
 #undef SF_TAIL
     }
@@ -792,6 +886,7 @@ struct OpsImpl {
         SolverCtx k{};
         if (ctx) k = *ctx;
         if (c.pipe && !pipe_ok(c)) return cudaErrorInvalidValue;
+        if (red == RED_CG && (!dag || !std::is_same<PV, PH>::value || !ctx || zv.v)) return cudaErrorInvalidValue;
         SF_NR_SWITCH(c.NR, {
             if constexpr (NR_ <= 2 && !std::is_same<PH, P64>::value) {
                 if (c.pipe) {
@@ -827,34 +922,32 @@ struct OpsImpl {
     }
     static int iteration_kernels(const LaunchCfg&) { return 10; }
 
-    // ---- one CG iteration on A = Dhat Dhat^dag (Hermitian, positive) for every
-    // active rhs:
-    //   t = Dhat^dag p; q = Dhat t (in v), <p, q> -> alpha = rho / <p, q>;
-    //   x += alpha p, r -= alpha q, |r|^2 -> beta = |r|^2 / rho;
-    //   p = r + beta p (the BiCGStab p update with omega = 0; sets the loop
-    //   condition).  8 kernels.
+    // ---- one CG step on A = Dhat Dhat^dag (Hermitian, positive) for every
+    // active rhs, in the single-reduction form (k_cg_step):
+    //   tmp = H^dag r; t = Dhat^dag r with |r|^2, |t|^2 = <r, A r> (opens the
+    //   step, sets the loop condition); tmp = H t; w = Dhat t (in v);
+    //   k_cg_step (alpha, beta; p, s, x, r).  5 kernels.
     static cudaError_t iterate_cg(const LaunchCfg& c, bool, const IterFields& f, const SolverCtx* ctx,
                                   cudaStream_t st) {
         const FieldPtr none{nullptr, nullptr};
         const bool copy = !std::is_same<PV, PH>::value;
         if (copy) return cudaErrorInvalidValue;  // CG runs with FP32 (or FP64) hop operands
         cudaError_t e;
-        if ((e = hop(c, 1, true, f.p, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
-        if ((e = tail(c, 0, true, RED_NONE, f.tmp, f.p, none, f.t, none, 1.0, -1.0, 2, ctx, nullptr, st)) !=
+        if ((e = hop(c, 1, true, f.r, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
+        if ((e = tail(c, 0, true, RED_CG, f.tmp, f.r, none, f.t, none, 1.0, -1.0, 2, ctx, nullptr, st)) !=
             cudaSuccess)
             return e;
         if ((e = hop(c, 1, false, f.t, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
-        if ((e = tail(c, 0, false, RED_R0V, f.tmp, f.t, none, f.v, f.p, 1.0, -1.0, 2, ctx, nullptr, st)) !=
+        if ((e = tail(c, 0, false, RED_NONE, f.tmp, f.t, none, f.v, none, 1.0, -1.0, 2, ctx, nullptr, st)) !=
             cudaSuccess)
             return e;
         SF_NR_SWITCH(c.NR, {
-            launch_pdl(k_cg_update<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
-                       wf<PV>(f.x), wf<PV>(f.r), cf<PV>(f.p), cf<PV>(f.v), *ctx);
+            launch_pdl(k_cg_step<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
+                       wf<PV>(f.x), wf<PV>(f.r), wf<PV>(f.p), wf<PV>(f.s), cf<PV>(f.v), *ctx);
         });
-        launch_finish<1, typename AccOf<typename PV::real>::T, FIN_CG, typename PV::real>(c, *ctx, nullptr, 0, st);
-        return p_update(c, f.p, f.ph, f.r, f.v, ctx, st);
+        return cudaGetLastError();
     }
-    static int iteration_kernels_cg(const LaunchCfg&) { return 8; }
+    static int iteration_kernels_cg(const LaunchCfg&) { return 5; }
 
     static cudaError_t init(const LaunchCfg& c, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
                             FieldPtr ph, const SolverCtx* ctx, int maxiter, cudaStream_t st) {

@@ -12,10 +12,14 @@ namespace sf {
 
 enum class Prec : int { F64 = 0, F32 = 1, F16 = 2 };
 
-// reductions fused into the tail of a D-hat application
-enum Red : int { RED_NONE = 0, RED_R0V = 1, RED_TS = 2, RED_NORM = 3 };
+// reductions fused into the tail of a D-hat application (RED_CG: |x|^2 of
+// the tail's x operand and |out|^2, and the start of a CG step: see k_tail)
+enum Red : int { RED_NONE = 0, RED_R0V = 1, RED_TS = 2, RED_NORM = 3, RED_CG = 4 };
 
-// Per (lattice, rhs) state of one BiCGStab iteration, in device memory.
+// Per (lattice, rhs) state of one Krylov iteration, in device memory.  CG
+// keeps gamma = |r|^2 in rho.x and its step length in alpha.x; the *_prev
+// fields are the copies the CG step reads while its first block of each
+// lattice writes the new values.
 struct KState {
     double2 rho, alpha, omega, beta;
     float2 alpha_f, omega_f, beta_f;  // the same coefficients for the FP32 kernels
@@ -25,6 +29,8 @@ struct KState {
     int iters;        // iterations done in this inner solve
     int maxiter;      // inner cap
     int flags;        // bit 0: breakdown (rho or <r0,v> = 0), bit 1: omega = 0
+    double gamma_prev, alpha_prev;  // CG: gamma and alpha of the previous step
+    int active_prev, iters_prev;    // CG: active and iters before the current step
 };
 
 // Per (lattice, rhs) state of the FP64 defect-correction loop.
@@ -104,7 +110,8 @@ struct KrylovOps {
     // number of kernels it launches
     cudaError_t (*iterate)(const LaunchCfg&, bool dag, const IterFields&, const SolverCtx*, cudaStream_t);
     int (*iteration_kernels)(const LaunchCfg&);
-    // CG on Dhat Dhat^dag (the normal-equation route): start and one iteration
+    // CG on Dhat Dhat^dag (the normal-equation route): start and one step
+    // (single-reduction form; its second kernel sets the loop condition)
     cudaError_t (*init_cg)(const LaunchCfg&, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
                            FieldPtr ph, const SolverCtx*, int maxiter, cudaStream_t);
     cudaError_t (*iterate_cg)(const LaunchCfg&, bool dag, const IterFields&, const SolverCtx*, cudaStream_t);
