@@ -110,11 +110,20 @@ typedef enum {
      * (= gamma5 Dhat^dag Dhat gamma5; FP32 inner, FP64 outer defect correction
      * on that system), X = Dhat^dag Y in FP64.  |phi - Dhat X| is the outer
      * residual CG is driven to; |X - Dhat^dag Y| is at rounding level. */
-    SF_SOLVE_CG_NORMAL = 5
+    SF_SOLVE_CG_NORMAL = 5,
+    /* the paper's mixed-precision-preconditioned Gl-BiCGStab (Sec. 3.2, case
+     * D1 of Table 1): BiCGStab in FP64 on the whole block with scalars from
+     * Frobenius inner products, right-preconditioned by FP32 BiCGStab solves
+     * of the single systems (relative residual 1e-5 each, all rhs in one
+     * launch); restarted from the recomputed FP64 residual while a rhs is
+     * above tol.  iters_outer reports the preconditioner calls, iters_inner
+     * the FP32 iterations.  One lattice only (not batches). */
+    SF_SOLVE_GL_BICGSTAB = 6
 } sf_algo;
 
 typedef struct {
-    int iters_outer;                   /* FP64 sweeps of the X solve (max over rhs) */
+    int iters_outer;                   /* FP64 sweeps of the X solve (max over rhs); Gl-BiCGStab:
+                                          its preconditioner calls */
     int iters_inner;                   /* inner iterations of the X solve (max over rhs) */
     int iters_outer_y;                 /* same for the Y solve (0 if Y was not asked for) */
     int iters_inner_y;

@@ -26,7 +26,8 @@ STATUS = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOMEM", 3: "SF_ECUDA", 4: "SF_ENOC
           6: "SF_ENOTSU3"}
 OPS = {"dhat": 0, "dhat_dag": 1, "dhatdag_dhat": 2, "d_full": 3, "hop_eo": 4, "hop_oe": 5}
 PRECS = {"fp64": 0, "fp32": 1, "fp16": 2}
-ALGOS = {"bicgstab": 0, "mixed_dc": 1, "mixed_dc_half": 2, "fgcr_cnn": 3, "fgcr": 4, "cg_normal": 5}
+ALGOS = {"bicgstab": 0, "mixed_dc": 1, "mixed_dc_half": 2, "fgcr_cnn": 3, "fgcr": 4, "cg_normal": 5,
+         "gl_bicgstab": 6}
 
 
 class SFError(RuntimeError):

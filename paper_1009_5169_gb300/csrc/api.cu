@@ -498,6 +498,17 @@ struct Workspace {
 
     Result fgcr(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
 
+    // ---- Gl-BiCGStab (FP64, Frobenius inner products over the block) with
+    // FP32-inner BiCGStab solves as its preconditioner
+    struct Gl {
+        FieldBuf r, r0, p, v, s, t, ph, sh;
+        DevMem ptrs, coef, dots;
+    };
+    std::unique_ptr<Gl> gl;
+    void precondition(bool dag, const FieldBuf& in, FieldBuf& out, double delta, int maxiter,
+                      std::vector<int>& iters);
+    Result gl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
+
     // per-rhs |b - A x| / |b| in FP64 (A = Dhat, or Dhat^dag for dag)
     std::vector<double> rel_residual(bool dag, const FieldBuf& b, const FieldBuf& x) {
         ensure_cfg(0);
@@ -897,6 +908,216 @@ Workspace::Result Workspace::fgcr(bool use_cnn, bool dag, const FieldBuf& phi, F
     return res;
 }
 
+// ---------------------------------------------------------------- Gl-BiCGStab
+// out = M in, the preconditioner of the Gl-BiCGStab outer solver: for each rhs
+// one FP32-inner BiCGStab solve of Dhat e = in_i / |in_i| (dag: Dhat^dag) from
+// e = 0 to relative residual delta, out_i = |in_i| e (the whole block in one
+// graph launch, the rhs independent of each other).  iters[i] += the inner
+// iterations of rhs i.
+void Workspace::precondition(bool dag, const FieldBuf& in, FieldBuf& out, double delta, int maxiter,
+                             std::vector<int>& iters) {
+    const int ci = 1;
+    ensure_cfg(0);
+    ensure_cfg(ci);
+    ensure_inner(ci);
+    const KrylovOps& o = ops_for(ci);
+    cudaStream_t s = stream;
+    const size_t n = (size_t)nlat * nrhs;
+    // one "sweep" of the outer check with tol2 = 0: active where in_i != 0,
+    // inv_norm = 1 / |in_i|, inner target delta
+    std::vector<OState> oh(n);
+    for (auto& e : oh) {
+        memset(&e, 0, sizeof e);
+        e.bb = 1.0;
+        e.delta2_floor = delta * delta;
+    }
+    CK(cudaMemcpyAsync(ost.p, oh.data(), n * sizeof(OState), cudaMemcpyHostToDevice, s));
+    SolverCtx k0 = ctx(false);
+    CK(launch_norm2(cfg[0].lc, in.ptr(), &k0, nrm_rr.as<double>(), s));
+    CK(launch_outer_check((int)n, ost.as<OState>(), nrm_rr.as<double>(), nullptr, 1, n_active.as<int>(), s));
+    CK(cudaMemsetAsync(out.v.p, 0, field_bytes(Prec::F64, S), s));
+    launches += 3;
+    GraphEntry& ge = graph(ci, dag, false);
+    CK(cudaStreamSynchronize(s));  // pin[] is rewritten below
+    pin[2] = maxiter + 8;
+    pin[5] = 0;
+    CK(cudaMemcpyAsync(loop_count.as<int>() + 1, pin + 2, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(loop_count.as<int>() + 3, pin + 5, sizeof(int), cudaMemcpyHostToDevice, s));
+    SolverCtx k = ctx(true);
+    CK(o.init(cfg[ci].lc, in.ptr(), inner[ci].x.ptr(), inner[ci].r.ptr(), inner[ci].r0.ptr(), inner[ci].p.ptr(),
+              inner[ci].ph.ptr(), &k, maxiter, s));
+    if (no_graph()) {
+        for (;;) {
+            enqueue_iteration(ci, dag, k, s, false);
+            CK(cudaMemcpyAsync(pin + 3, loop_count.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (!pin[3]) break;
+        }
+    } else {
+        CK(cudaGraphLaunch(ge.exec, s));
+    }
+    CK(o.dc_update(cfg[ci].lc, out.ptr(), inner[ci].x.ptr(), &k, s));
+    launches += 3;
+    std::vector<OState> oo(n);
+    CK(cudaMemcpyAsync(oo.data(), ost.p, n * sizeof(OState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pin + 5, loop_count.as<int>() + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    launches += (long long)o.iteration_kernels(cfg[ci].lc) * pin[5];
+    for (size_t i = 0; i < n; ++i) iters[i] += oo[i].inner_iters;
+}
+
+// Gl-BiCGStab (Jbilou, Sadok and Tinzefte 2005) on the block Dhat X = Phi
+// (dag: Dhat^dag) in FP64, right-preconditioned by M (precondition(): FP32
+// BiCGStab solves of the single systems, Sec. 3.2): BiCGStab whose scalars
+// come from the Frobenius inner products <A, B>_F = sum_i <a_i, b_i> of the
+// whole block, so that one alpha, omega, beta serve all right-hand sides and
+// the preconditioner calls are independent per rhs (Sec. 3.2).  Stops when
+// every rhs's recursive residual is below tol / 2 (at the half step after
+// alpha as well), then judges on the recomputed FP64 residual and restarts
+// from it while some rhs is above tol.  Result: sweeps = preconditioner
+// calls, inner = FP32 iterations per rhs.
+Workspace::Result Workspace::gl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
+    REQUIRE(nlat == 1, "Gl-BiCGStab runs on a single lattice");
+    ensure_cfg(0);
+    ensure_cfg(1);
+    ensure_cfg(3);
+    cudaStream_t s = stream;
+    const int n = nrhs;
+    const size_t fbytes = field_bytes(Prec::F64, S);
+    if (!gl) {
+        gl.reset(new Gl());
+        FieldBuf* f[8] = {&gl->r, &gl->r0, &gl->p, &gl->v, &gl->s, &gl->t, &gl->ph, &gl->sh};
+        std::vector<void*> p(8);
+        for (int k = 0; k < 8; ++k) {
+            f[k]->alloc(Prec::F64, S);
+            p[k] = f[k]->v.p;
+        }
+        gl->ptrs.ensure(p.size() * sizeof(void*));
+        CK(cudaMemcpy(gl->ptrs.p, p.data(), p.size() * sizeof(void*), cudaMemcpyHostToDevice));
+        gl->coef.ensure((size_t)2 * n * sizeof(double2));
+        gl->dots.ensure((size_t)n * sizeof(double2));
+    }
+    enum { kR = 0, kR0, kP, kV, kS, kT, kPH, kSH };
+    const double2* const* ptr = gl->ptrs.as<const double2*>();
+    const LaunchCfg& bl = cfg[3].lc;
+    std::vector<double2> hd(n), hc((size_t)2 * n);
+    auto dots = [&](const FieldBuf& a, const FieldBuf& b) {
+        dots64(a, b, gl->dots.as<double2>(), s);
+        CK(cudaMemcpyAsync(hd.data(), gl->dots.p, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    };
+    auto frob = [&](const FieldBuf& a, const FieldBuf& b) {
+        dots(a, b);
+        double2 z = make_double2(0.0, 0.0);
+        for (int i = 0; i < n; ++i) {
+            z.x += hd[i].x;
+            z.y += hd[i].y;
+        }
+        return z;
+    };
+    // y += c0 xs[k] (+ c1 xs[k + 1]), the same coefficients for every rhs
+    auto axpy = [&](int k, int nvec, double2 c0, double2 c1, FieldBuf& y) {
+        for (int i = 0; i < n; ++i) {
+            hc[i] = c0;
+            hc[(size_t)n + i] = c1;
+        }
+        CK(cudaMemcpyAsync(gl->coef.p, hc.data(), (size_t)nvec * n * sizeof(double2), cudaMemcpyHostToDevice, s));
+        CK(launch_multi_axpy64(bl, nvec, ptr + k, gl->coef.as<double2>(), y.ptr(), s));
+        launches += 1;
+    };
+    auto copy = [&](const FieldBuf& from, FieldBuf& to) {
+        CK(cudaMemcpyAsync(to.v.p, from.v.p, fbytes, cudaMemcpyDeviceToDevice, s));
+    };
+    auto cdiv = [](double2 a, double2 b) {
+        const double d = b.x * b.x + b.y * b.y;
+        return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+    };
+    auto cmul = [](double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
+    auto neg = [](double2 a) { return make_double2(-a.x, -a.y); };
+    const double2 zero = make_double2(0.0, 0.0);
+    const double delta = 1e-5;  // inner relative residual of a preconditioner call (the FP32 floor)
+    const int max_outer = 100, max_restarts = 4;
+
+    CK(cudaMemsetAsync(x.v.p, 0, fbytes, s));
+    copy(phi, gl->r);
+    dots(phi, phi);
+    std::vector<double> bb(n);
+    for (int i = 0; i < n; ++i) bb[i] = hd[i].x;
+    const double stop2 = 0.25 * tol * tol;  // recursive residual target (tol / 2)
+    auto below = [&](const FieldBuf& res) {  // every rhs's |res_i|^2 <= stop2 |phi_i|^2
+        dots(res, res);
+        for (int i = 0; i < n; ++i)
+            if (!(hd[i].x <= stop2 * bb[i])) return false;
+        return true;
+    };
+    Result res;
+    res.sweeps.assign(n, 0);
+    res.inner.assign(n, 0);
+    res.resid.assign(n, 0.0);
+    int calls = 0;
+    std::vector<double> rt(n);
+    for (int cycle = 0;; ++cycle) {
+        copy(gl->r, gl->r0);
+        copy(gl->r, gl->p);
+        double2 rho = frob(gl->r0, gl->r);
+        bool done = below(gl->r);
+        for (int it = 0; it < max_outer && !done && rho.x != 0.0; ++it) {
+            precondition(dag, gl->p, gl->ph, delta, maxiter, res.inner);
+            ++calls;
+            apply_dhat64(dag, gl->ph, gl->v, s);
+            const double2 r0v = frob(gl->r0, gl->v);
+            if (r0v.x == 0.0 && r0v.y == 0.0) break;
+            const double2 alpha = cdiv(rho, r0v);
+            copy(gl->r, gl->s);
+            axpy(kV, 1, neg(alpha), zero, gl->s);  // s = r - alpha v
+            if (below(gl->s)) {
+                axpy(kPH, 1, alpha, zero, x);
+                done = true;
+                break;
+            }
+            precondition(dag, gl->s, gl->sh, delta, maxiter, res.inner);
+            ++calls;
+            apply_dhat64(dag, gl->sh, gl->t, s);
+            const double2 ts = frob(gl->t, gl->s);
+            const double2 tt = frob(gl->t, gl->t);
+            if (tt.x == 0.0) break;
+            const double2 omega = make_double2(ts.x / tt.x, ts.y / tt.x);
+            axpy(kPH, 2, alpha, omega, x);  // x += alpha ph + omega sh
+            copy(gl->s, gl->r);
+            axpy(kT, 1, neg(omega), zero, gl->r);  // r = s - omega t
+            if (below(gl->r)) {
+                done = true;
+                break;
+            }
+            if (omega.x == 0.0 && omega.y == 0.0) break;
+            const double2 rho1 = frob(gl->r0, gl->r);
+            const double2 beta = cmul(cdiv(rho1, rho), cdiv(alpha, omega));
+            rho = rho1;
+            axpy(kV, 1, neg(omega), zero, gl->p);  // p - omega v
+            copy(gl->r, gl->s);
+            axpy(kP, 1, beta, zero, gl->s);  // r + beta (p - omega v)
+            copy(gl->s, gl->p);
+        }
+        // judge on the recomputed FP64 residual; restart from it while above tol
+        residual64(dag, phi, x, s);
+        CK(cudaMemcpyAsync(rt.data(), nrm_rr.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        bool ok = true;
+        for (int i = 0; i < n; ++i)
+            if (!(rt[i] <= tol * tol * bb[i]) && bb[i] > 0.0) ok = false;
+        if (ok || cycle + 1 >= max_restarts) {
+            res.converged = ok;
+            break;
+        }
+        copy(r64, gl->r);
+    }
+    for (int i = 0; i < n; ++i) {
+        res.sweeps[i] = calls;
+        res.resid[i] = bb[i] > 0 ? sqrt(rt[i] / bb[i]) : 0.0;
+    }
+    return res;
+}
+
 // ---------------------------------------------------------------- helpers
 namespace {
 
@@ -1195,6 +1416,7 @@ int algo_index(sf_algo a) {
         case SF_SOLVE_FGCR_CNN: return 3;
         case SF_SOLVE_FGCR: return 4;
         case SF_SOLVE_CG_NORMAL: return 5;
+        case SF_SOLVE_GL_BICGSTAB: return 6;
     }
     throw SfError{SF_EINVAL, "bad algorithm"};
 }
@@ -1211,12 +1433,12 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         const int ci = algo_index(algo);
-        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5);
+        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5), glb = (ci == 6);
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.launches = 0;
         w.ensure_cfg(0);
-        if (!fgcr) w.ensure_cfg(normal ? 1 : ci);
+        if (!fgcr) w.ensure_cfg(normal || glb ? 1 : ci);
         cudaStream_t s = lat->stream;
         const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
         const LaunchCfg& pl = w.cfg[0].per_lat[0];
@@ -1224,6 +1446,7 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         CK(ops_f64().pack(pl, dphi, w.phi64.ptr(), s));
         w.launches += 1;
         auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol) {
+            if (glb) return w.gl_bicgstab(dag, rhs, sol, tol, maxiter);
             return fgcr ? w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter) : w.solve(ci, dag, rhs, sol, tol, maxiter);
         };
         Workspace::Result rx, ry;
@@ -1335,12 +1558,12 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         const int ci = algo_index(algo);
-        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5);
+        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5), glb = (ci == 6);
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.launches = 0;
         w.ensure_cfg(0);
-        if (!fgcr) w.ensure_cfg(normal ? 1 : ci);
+        if (!fgcr) w.ensure_cfg(normal || glb ? 1 : ci);
         ensure_odd(w);
         cudaStream_t s = lat->stream;
         const KrylovOps& o = ops_f64();
@@ -1351,8 +1574,9 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         w.launches += 1;
         // X = Dhat^-1 phi and its odd part; Y = Dhat^-dag X and its odd part
         auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol, FieldBuf& odd) {
-            if (!fgcr) return w.solve(ci, dag, rhs, sol, tol, maxiter, false, &odd);
-            Workspace::Result r = w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter);
+            if (!fgcr && !glb) return w.solve(ci, dag, rhs, sol, tol, maxiter, false, &odd);
+            Workspace::Result r =
+                glb ? w.gl_bicgstab(dag, rhs, sol, tol, maxiter) : w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter);
             CK(o.hop(w.cfg[0].lc, 1, dag, sol.ptr(), odd.ptr(), 1.0, 1, nullptr, s));
             w.launches += 1;
             return r;
