@@ -319,8 +319,9 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             return (time.perf_counter() - t0) / reps, inf
         comparators = {}
-        for algo in ("bicgstab", "mixed_dc", "mixed_dc_half", "cg_normal", "gl_bicgstab"):
-            # gl_bicgstab: the paper's D1 solver; its "sweeps" are preconditioner calls
+        for algo in ("bicgstab", "mixed_dc", "mixed_dc_half", "cg_normal", "gl_bicgstab", "bl_bicgstab"):
+            # gl_bicgstab: the paper's D1 solver, its "sweeps" are preconditioner calls;
+            # bl_bicgstab: the paper's case C, its "inner_iters" are block iterations
             t, inf = time_solve(algo, phi_d, X_d, Y_d)
             comparators[f"{algo}_block{nrhs}"] = {
                 "ms": round(t * 1e3, 3), "sweeps": [inf["iters_outer"], inf["iters_outer_y"]],

@@ -118,7 +118,13 @@ typedef enum {
      * launch); restarted from the recomputed FP64 residual while a rhs is
      * above tol.  iters_outer reports the preconditioner calls, iters_inner
      * the FP32 iterations.  One lattice only (not batches). */
-    SF_SOLVE_GL_BICGSTAB = 6
+    SF_SOLVE_GL_BICGSTAB = 6,
+    /* Bl-BiCGStab in FP64 (the paper's case C, Sec. 3.2): the rhs share one
+     * Krylov space through nrhs x nrhs coefficient matrices; restarted from
+     * the recomputed FP64 residual while a rhs is above tol.  iters_inner
+     * reports the block iterations (each applies Dhat to every rhs twice),
+     * iters_outer the restarts + 1.  One lattice only (not batches). */
+    SF_SOLVE_BL_BICGSTAB = 7
 } sf_algo;
 
 typedef struct {

@@ -27,7 +27,7 @@ STATUS = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOMEM", 3: "SF_ECUDA", 4: "SF_ENOC
 OPS = {"dhat": 0, "dhat_dag": 1, "dhatdag_dhat": 2, "d_full": 3, "hop_eo": 4, "hop_oe": 5}
 PRECS = {"fp64": 0, "fp32": 1, "fp16": 2}
 ALGOS = {"bicgstab": 0, "mixed_dc": 1, "mixed_dc_half": 2, "fgcr_cnn": 3, "fgcr": 4, "cg_normal": 5,
-         "gl_bicgstab": 6}
+         "gl_bicgstab": 6, "bl_bicgstab": 7}
 
 
 class SFError(RuntimeError):

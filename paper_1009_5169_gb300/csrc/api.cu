@@ -16,6 +16,7 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -508,6 +509,12 @@ struct Workspace {
     void precondition(bool dag, const FieldBuf& in, FieldBuf& out, double delta, int maxiter,
                       std::vector<int>& iters);
     Result gl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
+    DevMem gram_partials, gram_out, bcoef;
+    // G[i][j] = <a_i, b_j> (one lattice) -> host, row-major s x s
+    void gram64(const FieldBuf& a, const FieldBuf& b, std::vector<std::complex<double>>& G);
+    // y_j += sum_i x_i C[i][j] (C row-major s x s, host)
+    void block_axpy64(const FieldBuf& x, const std::vector<std::complex<double>>& C, FieldBuf& y);
+    Result bl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
 
     // per-rhs |b - A x| / |b| in FP64 (A = Dhat, or Dhat^dag for dag)
     std::vector<double> rel_residual(bool dag, const FieldBuf& b, const FieldBuf& x) {
@@ -1118,6 +1125,198 @@ Workspace::Result Workspace::gl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf
     return res;
 }
 
+// ---------------------------------------------------------------- Bl-BiCGStab
+namespace {
+// Solve A X = B for s x s complex A (row-major) and s x m B by Gaussian
+// elimination with partial pivoting; false if a pivot vanishes.
+bool small_solve(int s, std::vector<std::complex<double>> A, std::vector<std::complex<double>>& B, int m) {
+    for (int k = 0; k < s; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < s; ++i)
+            if (std::abs(A[i * s + k]) > std::abs(A[piv * s + k])) piv = i;
+        if (!(std::abs(A[piv * s + k]) > 0.0)) return false;
+        if (piv != k) {
+            for (int j = 0; j < s; ++j) std::swap(A[k * s + j], A[piv * s + j]);
+            for (int j = 0; j < m; ++j) std::swap(B[k * m + j], B[piv * m + j]);
+        }
+        for (int i = k + 1; i < s; ++i) {
+            const std::complex<double> f = A[i * s + k] / A[k * s + k];
+            for (int j = k; j < s; ++j) A[i * s + j] -= f * A[k * s + j];
+            for (int j = 0; j < m; ++j) B[i * m + j] -= f * B[k * m + j];
+        }
+    }
+    for (int k = s - 1; k >= 0; --k)
+        for (int j = 0; j < m; ++j) {
+            std::complex<double> v = B[k * m + j];
+            for (int i = k + 1; i < s; ++i) v -= A[k * s + i] * B[i * m + j];
+            B[k * m + j] = v / A[k * s + k];
+        }
+    return true;
+}
+}  // namespace
+
+void Workspace::gram64(const FieldBuf& a, const FieldBuf& b, std::vector<std::complex<double>>& G) {
+    const LaunchCfg& c = cfg[3].lc;
+    const int n = nrhs, S2 = (n <= 8) ? 16 : 32;
+    gram_partials.ensure((size_t)n * S2 * c.nblocks * sizeof(double));
+    gram_out.ensure((size_t)n * S2 * sizeof(double));
+    CK(launch_gram64(c, a.ptr(), b.ptr(), gram_partials.as<double>(), gram_out.as<double>(), stream));
+    launches += 2;
+    std::vector<double> h((size_t)n * S2);
+    CK(cudaMemcpyAsync(h.data(), gram_out.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    G.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) G[(size_t)i * n + j] = {h[(size_t)j * S2 + 2 * i], h[(size_t)j * S2 + 2 * i + 1]};
+}
+
+void Workspace::block_axpy64(const FieldBuf& x, const std::vector<std::complex<double>>& C, FieldBuf& y) {
+    const int n = nrhs;
+    std::vector<double2> hc((size_t)n * n);
+    for (size_t k = 0; k < hc.size(); ++k) hc[k] = make_double2(C[k].real(), C[k].imag());
+    bcoef.ensure(hc.size() * sizeof(double2));
+    CK(cudaMemcpyAsync(bcoef.p, hc.data(), hc.size() * sizeof(double2), cudaMemcpyHostToDevice, stream));
+    CK(launch_block_axpy64(cfg[3].lc, x.ptr(), bcoef.as<double2>(), y.ptr(), stream));
+    launches += 1;
+    CK(cudaStreamSynchronize(stream));  // hc leaves scope
+}
+
+// Bl-BiCGStab (El Guennouni, Jbilou and Sadok 2003) on the block Dhat X = Phi
+// (dag: Dhat^dag) in FP64, the blocked solver of the paper's case C (Sec. 3.2,
+// Table 1): the columns share one Krylov space through s x s coefficient
+// matrices,
+//   V = A P;  alpha = (R0^H V)^-1 (R0^H R);  S = R - V alpha;  T = A S;
+//   omega = <T, S>_F / <T, T>_F;  X += P alpha + omega S;  R = S - omega T;
+//   beta = -(R0^H V)^-1 (R0^H T);  P = R + (P - omega V) beta,
+// with R0 the initial residual block, the s x s systems solved on the host
+// by pivoted elimination.  Stops when every column's recursive residual is
+// below tol / 2 (also at the half step after alpha), judges on the
+// recomputed FP64 residual and restarts from it while a column is above tol.
+// Result: sweeps = restarts + 1, inner = block iterations (each applies A to
+// all s columns twice).
+Workspace::Result Workspace::bl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
+    REQUIRE(nlat == 1, "Bl-BiCGStab runs on a single lattice");
+    ensure_cfg(0);
+    ensure_cfg(3);
+    cudaStream_t s = stream;
+    const int n = nrhs;
+    const size_t fbytes = field_bytes(Prec::F64, S);
+    if (!gl) {
+        gl.reset(new Gl());
+        FieldBuf* f[8] = {&gl->r, &gl->r0, &gl->p, &gl->v, &gl->s, &gl->t, &gl->ph, &gl->sh};
+        std::vector<void*> p(8);
+        for (int k = 0; k < 8; ++k) {
+            f[k]->alloc(Prec::F64, S);
+            p[k] = f[k]->v.p;
+        }
+        gl->ptrs.ensure(p.size() * sizeof(void*));
+        CK(cudaMemcpy(gl->ptrs.p, p.data(), p.size() * sizeof(void*), cudaMemcpyHostToDevice));
+        gl->coef.ensure((size_t)2 * n * sizeof(double2));
+        gl->dots.ensure((size_t)n * sizeof(double2));
+    }
+    using cd = std::complex<double>;
+    std::vector<double2> hd(n);
+    auto dots = [&](const FieldBuf& a, const FieldBuf& b) {
+        dots64(a, b, gl->dots.as<double2>(), s);
+        CK(cudaMemcpyAsync(hd.data(), gl->dots.p, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    };
+    auto copy = [&](const FieldBuf& from, FieldBuf& to) {
+        CK(cudaMemcpyAsync(to.v.p, from.v.p, fbytes, cudaMemcpyDeviceToDevice, s));
+    };
+    auto diag = [&](cd w) {  // w times the identity
+        std::vector<cd> D((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i) D[(size_t)i * n + i] = w;
+        return D;
+    };
+    CK(cudaMemsetAsync(x.v.p, 0, fbytes, s));
+    copy(phi, gl->r);
+    dots(phi, phi);
+    std::vector<double> bb(n);
+    for (int i = 0; i < n; ++i) bb[i] = hd[i].x;
+    const double stop2 = 0.25 * tol * tol;
+    auto below = [&](const FieldBuf& res) {
+        dots(res, res);
+        for (int i = 0; i < n; ++i)
+            if (!(hd[i].x <= stop2 * bb[i])) return false;
+        return true;
+    };
+    Result res;
+    res.sweeps.assign(n, 0);
+    res.inner.assign(n, 0);
+    res.resid.assign(n, 0.0);
+    const int max_restarts = 4;
+    int iters = 0, cycles = 0;
+    std::vector<double> rt(n);
+    std::vector<cd> M, Q, N;
+    for (int cycle = 0;; ++cycle) {
+        ++cycles;
+        copy(gl->r, gl->r0);
+        copy(gl->r, gl->p);
+        bool done = below(gl->r);
+        while (!done && iters < maxiter) {
+            apply_dhat64(dag, gl->p, gl->v, s);
+            gram64(gl->r0, gl->v, M);
+            gram64(gl->r0, gl->r, Q);
+            std::vector<cd> alpha = Q;
+            if (!small_solve(n, M, alpha, n)) break;
+            ++iters;
+            copy(gl->r, gl->s);
+            std::vector<cd> na(alpha);
+            for (auto& z : na) z = -z;
+            block_axpy64(gl->v, na, gl->s);  // S = R - V alpha
+            if (below(gl->s)) {
+                block_axpy64(gl->p, alpha, x);
+                done = true;
+                break;
+            }
+            apply_dhat64(dag, gl->s, gl->t, s);
+            dots(gl->t, gl->s);
+            cd ts = 0.0;
+            for (int i = 0; i < n; ++i) ts += cd(hd[i].x, hd[i].y);
+            dots(gl->t, gl->t);
+            double tt = 0.0;
+            for (int i = 0; i < n; ++i) tt += hd[i].x;
+            if (!(tt > 0.0)) break;
+            const cd omega = ts / tt;
+            block_axpy64(gl->p, alpha, x);
+            block_axpy64(gl->s, diag(omega), x);  // X += P alpha + omega S
+            copy(gl->s, gl->r);
+            block_axpy64(gl->t, diag(-omega), gl->r);  // R = S - omega T
+            if (below(gl->r)) {
+                done = true;
+                break;
+            }
+            if (omega == 0.0) break;
+            gram64(gl->r0, gl->t, N);
+            std::vector<cd> beta = N;
+            for (auto& z : beta) z = -z;
+            if (!small_solve(n, M, beta, n)) break;
+            block_axpy64(gl->v, diag(-omega), gl->p);  // P - omega V
+            copy(gl->r, gl->ph);
+            block_axpy64(gl->p, beta, gl->ph);  // R + (P - omega V) beta
+            copy(gl->ph, gl->p);
+        }
+        residual64(dag, phi, x, s);
+        CK(cudaMemcpyAsync(rt.data(), nrm_rr.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        bool ok = true;
+        for (int i = 0; i < n; ++i)
+            if (!(rt[i] <= tol * tol * bb[i]) && bb[i] > 0.0) ok = false;
+        if (ok || cycle + 1 >= max_restarts || iters >= maxiter) {
+            res.converged = ok;
+            break;
+        }
+        copy(r64, gl->r);
+    }
+    for (int i = 0; i < n; ++i) {
+        res.sweeps[i] = cycles;
+        res.inner[i] = iters;
+        res.resid[i] = bb[i] > 0 ? sqrt(rt[i] / bb[i]) : 0.0;
+    }
+    return res;
+}
+
 // ---------------------------------------------------------------- helpers
 namespace {
 
@@ -1417,6 +1616,7 @@ int algo_index(sf_algo a) {
         case SF_SOLVE_FGCR: return 4;
         case SF_SOLVE_CG_NORMAL: return 5;
         case SF_SOLVE_GL_BICGSTAB: return 6;
+        case SF_SOLVE_BL_BICGSTAB: return 7;
     }
     throw SfError{SF_EINVAL, "bad algorithm"};
 }
@@ -1433,12 +1633,12 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         const int ci = algo_index(algo);
-        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5), glb = (ci == 6);
+        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5), glb = (ci == 6), blb = (ci == 7);
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.launches = 0;
         w.ensure_cfg(0);
-        if (!fgcr) w.ensure_cfg(normal || glb ? 1 : ci);
+        if (!fgcr && !blb) w.ensure_cfg(normal || glb ? 1 : ci);
         cudaStream_t s = lat->stream;
         const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
         const LaunchCfg& pl = w.cfg[0].per_lat[0];
@@ -1447,6 +1647,7 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         w.launches += 1;
         auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol) {
             if (glb) return w.gl_bicgstab(dag, rhs, sol, tol, maxiter);
+            if (blb) return w.bl_bicgstab(dag, rhs, sol, tol, maxiter);
             return fgcr ? w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter) : w.solve(ci, dag, rhs, sol, tol, maxiter);
         };
         Workspace::Result rx, ry;
@@ -1558,12 +1759,12 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         const int ci = algo_index(algo);
-        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5), glb = (ci == 6);
+        const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5), glb = (ci == 6), blb = (ci == 7);
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.launches = 0;
         w.ensure_cfg(0);
-        if (!fgcr) w.ensure_cfg(normal || glb ? 1 : ci);
+        if (!fgcr && !blb) w.ensure_cfg(normal || glb ? 1 : ci);
         ensure_odd(w);
         cudaStream_t s = lat->stream;
         const KrylovOps& o = ops_f64();
@@ -1574,9 +1775,10 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         w.launches += 1;
         // X = Dhat^-1 phi and its odd part; Y = Dhat^-dag X and its odd part
         auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol, FieldBuf& odd) {
-            if (!fgcr && !glb) return w.solve(ci, dag, rhs, sol, tol, maxiter, false, &odd);
-            Workspace::Result r =
-                glb ? w.gl_bicgstab(dag, rhs, sol, tol, maxiter) : w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter);
+            if (!fgcr && !glb && !blb) return w.solve(ci, dag, rhs, sol, tol, maxiter, false, &odd);
+            Workspace::Result r = glb   ? w.gl_bicgstab(dag, rhs, sol, tol, maxiter)
+                                  : blb ? w.bl_bicgstab(dag, rhs, sol, tol, maxiter)
+                                        : w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter);
             CK(o.hop(w.cfg[0].lc, 1, dag, sol.ptr(), odd.ptr(), 1.0, 1, nullptr, s));
             w.launches += 1;
             return r;

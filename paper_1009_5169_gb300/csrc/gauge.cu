@@ -436,6 +436,109 @@ __global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_multi_axpy64(const LatDev*
     }
 }
 
+// ------------------------------------------------------------ FP64 block BLAS for Bl-BiCGStab
+// Gram block G[i][j] = <a_i, b_j> (sum over the lattice of a_i^dag b_j) for
+// all pairs of rhs of one lattice: thread (site, j) loads b_j once and runs
+// over the a_i; per-block partials in the layout of block_partials with
+// "rhs" j and quantity q = 2 i + (re, im).
+template <int S>
+__global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_gram64(const LatDev* __restrict__ lats, int nlat, int nrhs,
+                                                           CField<P64> a, CField<P64> b, double* __restrict__ partials) {
+    pdl_enter();
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int j = threadIdx.y;
+    double red[1][2 * S];
+#pragma unroll
+    for (int q = 0; q < 2 * S; ++q) red[0][q] = 0.0;
+    if (j < nrhs) {
+        for (int tile = tile_begin(g), te = tile_end(g); tile < te; ++tile) {
+            const int cb = tile_cb(g, tile, threadIdx.x);
+            if (cb < 0) continue;
+            cpx<double> y[4][3];
+            load_spinor<P64, double>(b, vbase<P64>(g, j), g.Vpad, cb, 0, y);
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                if (i >= nrhs) break;
+                cpx<double> x[4][3];
+                load_spinor<P64, double>(a, vbase<P64>(g, i), g.Vpad, cb, 0, x);
+                dotc_acc(x, y, red[0][2 * i], red[0][2 * i + 1]);
+            }
+        }
+    }
+    block_partials<1, 2 * S>(red, nrhs, partials);
+}
+
+// the lattice sums of the Gram partials: out[(j * 2S + 2i) + (0, 1)] = G[i][j]
+// (one block, lattice 0)
+template <int S>
+__global__ void __launch_bounds__(FIN_THREADS) k_gram64_finish(const LatDev* __restrict__ lats, int nrhs,
+                                                               int nblocks, const double* __restrict__ partials,
+                                                               double* __restrict__ out) {
+    pdl_enter();
+    __shared__ double sres[MAX_RHS * 2 * S];
+    lattice_sums<2 * S, double>(partials, nrhs, nblocks, lats[0].blk0, lats[0].nblk, threadIdx.x, (int)blockDim.x,
+                                sres);
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrhs * 2 * S; r += blockDim.x) out[r] = sres[r];
+}
+
+// Y_j += sum_i X_i C[i * nrhs + j] for every column j (C an nrhs x nrhs
+// complex matrix, device; X and Y distinct fields)
+__global__ void __launch_bounds__(KB<P64, 1>::MAXT) k_block_axpy64(const LatDev* __restrict__ lats, int nlat,
+                                                                 int nrhs, const double2* __restrict__ x,
+                                                                 const double2* __restrict__ c,
+                                                                 double2* __restrict__ y) {
+    pdl_enter();
+    const int l = find_lattice(lats, nlat, blockIdx.x);
+    const LatDev g = lats[l];
+    const int j = threadIdx.y;
+    if (j >= nrhs) return;
+    for (int tile = tile_begin(g), te = tile_end(g); tile < te; ++tile) {
+        const int cb = tile_cb(g, tile, threadIdx.x);
+        if (cb < 0) continue;
+        const long long yb = vbase<P64>(g, j) + cb;
+        double2 acc[12];
+#pragma unroll
+        for (int comp = 0; comp < 12; ++comp) acc[comp] = y[yb + (long long)comp * g.Vpad];
+        for (int i = 0; i < nrhs; ++i) {
+            const double2 ci = c[i * nrhs + j];
+            const long long xb = vbase<P64>(g, i) + cb;
+#pragma unroll
+            for (int comp = 0; comp < 12; ++comp) {
+                const double2 xv = __ldg(x + xb + (long long)comp * g.Vpad);
+                acc[comp].x += ci.x * xv.x - ci.y * xv.y;
+                acc[comp].y += ci.x * xv.y + ci.y * xv.x;
+            }
+        }
+#pragma unroll
+        for (int comp = 0; comp < 12; ++comp) y[yb + (long long)comp * g.Vpad] = acc[comp];
+    }
+}
+
+cudaError_t launch_gram64(const LaunchCfg& c, FieldPtr a, FieldPtr b, double* partials, double* out,
+                          cudaStream_t st) {
+    if (c.nlat != 1 || c.nrhs > MAX_RHS) return cudaErrorInvalidValue;
+    if (c.nrhs <= 8) {
+        launch_pdl(k_gram64<8>, dim3(c.nblocks), dim3(dim3(c.TS, c.nrhs)), st, c.lats, c.nlat, c.nrhs, cf<P64>(a),
+                   cf<P64>(b), partials);
+        launch_pdl(k_gram64_finish<8>, dim3(1), dim3(FIN_THREADS), st, c.lats, c.nrhs, c.nblocks,
+                   (const double*)partials, out);
+    } else {
+        launch_pdl(k_gram64<16>, dim3(c.nblocks), dim3(dim3(c.TS, c.nrhs)), st, c.lats, c.nlat, c.nrhs, cf<P64>(a),
+                   cf<P64>(b), partials);
+        launch_pdl(k_gram64_finish<16>, dim3(1), dim3(FIN_THREADS), st, c.lats, c.nrhs, c.nblocks,
+                   (const double*)partials, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_axpy64(const LaunchCfg& c, FieldPtr x, const double2* coef, FieldPtr y, cudaStream_t st) {
+    launch_pdl(k_block_axpy64, dim3(c.nblocks), dim3(dim3(c.TS, c.nrhs)), st, c.lats, c.nlat, c.nrhs,
+               reinterpret_cast<const double2*>(x.v), coef, reinterpret_cast<double2*>(y.v));
+    return cudaGetLastError();
+}
+
 // out = gamma_5 in (spin components 2, 3 negated)
 __global__ void k_gamma5_64(long long n_per_rhs_planes, int Vpad, const double2* __restrict__ in, double2* __restrict__ out,
                             long long total) {

@@ -163,6 +163,12 @@ cudaError_t launch_dot64(const LaunchCfg&, FieldPtr a, FieldPtr b, const SolverC
 cudaError_t launch_multi_axpy64(const LaunchCfg&, int nvec, const double2* const* xs, const double2* coef, FieldPtr y,
                                 cudaStream_t);
 cudaError_t launch_gamma5_64(long long total_elems, int Vpad, FieldPtr in, FieldPtr out, cudaStream_t);
+// Gram block G[i][j] = <a_i, b_j> of one lattice's block vectors -> out
+// (device, out[j * 2S + 2 i + (0, 1)], S = 8 for nrhs <= 8 else 16); partials
+// holds nrhs * 2S * nblocks doubles
+cudaError_t launch_gram64(const LaunchCfg&, FieldPtr a, FieldPtr b, double* partials, double* out, cudaStream_t);
+// y_j += sum_i x_i coef[i * nrhs + j] (coef on the device; x, y distinct)
+cudaError_t launch_block_axpy64(const LaunchCfg&, FieldPtr x, const double2* coef, FieldPtr y, cudaStream_t);
 
 }  // namespace sf
 
