@@ -380,6 +380,30 @@ def run_ours(args, rank, world, local_rank):
         for bl in blats:
             bl.close()
 
+    # ---------------- one HMC trajectory around the MD step (same lattice and pseudo-fermion count)
+    hmc = None
+    if not args.no_hmc and rank == 0:
+        hlat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, U_d, device=local_rank)
+        P0 = torch.from_numpy(inputs.su3_directions(fshape[:2], inputs.SEED_BASE + 501)).to(dev)
+        eta = torch.from_numpy(inputs.sources(lt.L, lt.T, nrhs, inputs.SEED_BASE + 502)).to(dev)
+        hphi = torch.empty_like(eta)
+        sf.wilson_apply_block(hlat, "dhat", "fp64", eta, hphi)
+        nst, dt = 10, 0.02
+        sf.md_trajectory(hlat, args.algo, hphi, P0.clone(), 2, dt, tol=tol, maxiter=args.maxiter)  # warm-up
+        hlat.set_links(U_d)
+        mom_t = P0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hinfo = sf.md_trajectory(hlat, args.algo, hphi, mom_t, nst, dt, tol=tol, maxiter=args.maxiter)
+        torch.cuda.synchronize()
+        th = time.perf_counter() - t0
+        hmc = {"workload": f"{lt.L}^3x{lt.T} SF, {nrhs} pseudo-fermions phi = Dhat eta, Gaussian momenta, "
+                           f"leapfrog {nst} x dt {dt} (trajectory length {nst * dt:g}), {args.algo} to {tol}",
+               "ms": round(th * 1e3, 2), "force_evals": hinfo["force_evals"],
+               "ms_per_force_eval": round(th * 1e3 / hinfo["force_evals"], 3), "dH": hinfo["dH"],
+               "inner_iters": hinfo["inner_iters"], "kernel_launches": hinfo["kernel_launches"]}
+        hlat.close()
+
     learned = None
     if not args.no_learned and rank == 0:
         learned = learned_section(args, dev, local_rank, stream)
@@ -397,7 +421,7 @@ def run_ours(args, rank, world, local_rank):
                      "sweeps_y": last["iters_outer_y"], "inner_iters_y": last["iters_inner_y"],
                      "solve_block_recheck": recheck},
         "roofline": roofline, "dslash_hbm": hbm, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "comparators": comparators, "batched": batched, "learned": learned,
+        "comparators": comparators, "batched": batched, "hmc_trajectory": hmc, "learned": learned,
     }
     lat.close()
     if rank == 0 and not args.no_cpu_baseline:
@@ -606,6 +630,7 @@ def main():
     ap.add_argument("--no-hbm-case", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-hmc", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-train-fields", type=int, default=8)
     ap.add_argument("--learned-epochs", type=int, default=15)

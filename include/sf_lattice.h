@@ -209,6 +209,48 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
  * w = 1/2 for spatial plaquettes at x0 = 0 and x0 = T and 1 otherwise. */
 sf_status plaquette_action(sf_lattice* lat, double* S);
 
+/* ---- the HMC trajectory around Alg. 2 (the steps either side of the MD
+ * force: momenta, gauge force, link update, leapfrog).  Momenta and forces
+ * use the force layout [(T+1) L^3][4][8] (components along T^a = lambda^a/2);
+ * only the dynamic links move: U_0(x) for x0 = 0..T-1 and U_k(x) for
+ * x0 = 1..T-1 (the spatial boundary links at x0 = 0, T are fixed, with zero
+ * momentum and force). */
+
+/* The force of the plaquette action, F^a_mu(x) = dS_g/d omega^a for
+ * U_mu(x) -> exp(i omega^a T^a) U_mu(x): writes F (may be NULL) and, if mom
+ * is not NULL, does mom -= eps F. */
+sf_status gauge_force(sf_lattice* lat, double* F, double* mom, double eps);
+
+/* U_mu(x) <- exp(i dt P_mu(x)) U_mu(x) on the dynamic links (P = P^a T^a from
+ * mom), then the prepared link copies are rebuilt (no SU(3) re-check). */
+sf_status sf_lattice_update_links(sf_lattice* lat, const double* mom, double dt);
+
+/* Copy the lattice's current FP64 links out (canonical layout). */
+sf_status sf_lattice_get_links(sf_lattice* lat, double* links);
+
+typedef struct {
+    double kinetic[2];      /* sum_links,a (P^a)^2 / 2 at the start and the end */
+    double s_gauge[2];      /* plaquette action */
+    double s_fermion[2];    /* sum_i |Dhat^{-1} phi_i|^2 */
+    double dH;              /* H(end) - H(start) */
+    int force_evals;        /* fermion force evaluations (nsteps + 1) */
+    int inner_iters;        /* inner solver iterations summed over them (X and Y) */
+    double seconds;
+    long long kernel_launches;
+} sf_md_info;
+
+/* One leapfrog molecular-dynamics trajectory of nsteps steps of size dt:
+ * P -= dt/2 F(U); then nsteps times { U <- exp(i dt P) U; P -= dt F(U) },
+ * the last kick dt/2; F = gauge force + the fermion force of Alg. 2 for
+ * the pseudo-fermions phi (nrhs even-site fields, solved with algo to tol).
+ * The lattice's links and mom (in / out; its boundary entries are zeroed
+ * first) move; H = kinetic + S_g + S_f is reported at both ends, S_f from
+ * the X of the first and last force evaluations.  A Metropolis step is the
+ * caller's: accept with probability min(1, exp(-dH)), else restore the links
+ * with sf_lattice_set_links. */
+sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom, int nsteps,
+                           double dt, double tol, int maxiter, sf_md_info* info);
+
 /* One launch of the hopping-term kernel H_oe (out_parity 1) or H_eo
  * (out_parity 0) for nrhs fields in precision prec, on the lattice's
  * resident operand and result buffers (those wilson_apply_block last packed;

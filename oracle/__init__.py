@@ -14,8 +14,11 @@ Array conventions (numpy complex128):
 
 Parity pins: every function here is pinned by a ``-m "not gpu"`` test
 (free-field closed form, gamma_5-hermiticity, gauge covariance, theta-twist
-equivalence, Schur complement vs. dense LU, BiCGStab vs. dense LU, force vs.
-central finite differences, plaquette closed forms).
+equivalence, Schur complement vs. dense LU, BiCGStab vs. dense LU, force and
+gauge force vs. central finite differences, plaquette closed forms).
+``oracle.hmc`` adds the HMC trajectory around the MD step (momenta, link
+exponential, leapfrog), pinned by closed forms, the O(dt^2) energy error and
+reversibility.
 """
 from __future__ import annotations
 
@@ -67,6 +70,7 @@ def lib() -> ctypes.CDLL:
             L.sfo_bicgstab.argtypes = [i, i, d, d, dp, i, i, dp, dp, d, i, ip, dp]
             L.sfo_force.argtypes = [i, i, d, d, dp, i, dp, dp, dp]
             L.sfo_plaquette_action.argtypes = [i, i, d, dp]
+            L.sfo_gauge_force.argtypes = [i, i, d, dp, dp]
             L.sfo_plaquette_action.restype = d
             L.sfo_num_threads.restype = i
             L.sfo_set_num_threads.argtypes = [i]
@@ -167,6 +171,16 @@ def force(U, X_e, Y_e, L, T, theta, kappa):
 def plaquette_action(U, L, T, beta):
     """SF Wilson plaquette action S_g = beta sum_p w(p) (1 - Re tr U_p / 3)."""
     return float(lib().sfo_plaquette_action(L, T, beta, _p(_c(U))))
+
+
+def gauge_force(U, L, T, beta):
+    """Force of the SF plaquette action, F^a_mu(x) = dS_g/d omega^a for
+    U_mu(x) -> exp(i omega^a T^a) U_mu(x); zero on the fixed boundary links.
+    Shape [(T+1)L^3, 4, 8]."""
+    F = np.zeros(((T + 1) * L ** 3, 4, 8), np.float64)
+    rc = lib().sfo_gauge_force(L, T, beta, _p(_c(U)), _p(F))
+    assert rc == 0
+    return F
 
 
 # ---------------------------------------------------------------- helpers

@@ -19,7 +19,8 @@
  *   - the MD force F_mu(n) = sum_i f[x_i, y_i] of Eq. (3) with x = Dhat^-1 phi,
  *     y = Dhat^-dag x (Alg. 2), written as the exact gradient of
  *     S = sum_i |Dhat^-1 phi_i|^2 (Eq. 2);
- *   - the SU(3) plaquette action with SF boundary weights (Sec. 4).
+ *   - the SU(3) plaquette action with SF boundary weights (Sec. 4) and its
+ *     force (the gauge part of the HMC trajectory the MD step belongs to).
  *
  * Readings of the paper (it fixes none of these):
  *   - gamma matrices: Euclidean, Hermitian, chiral basis; gamma_5 =
@@ -653,6 +654,93 @@ double sfo_plaquette_action(int L, int T, double beta, const double* Ud)
             }
     }
     return beta * S;
+}
+
+/* ------------------------------------------------------ gauge force */
+
+/* weight of the plaquette with base y0 in the plane {mu, nu} (0 if it is not
+ * part of the action): the rules of sfo_plaquette_action */
+static double plaq_weight(int T, int y0, int mu, int nu)
+{
+    if (y0 < 0 || y0 > T) return 0.0;
+    if (mu == 0 || nu == 0) return (y0 <= T - 1) ? 1.0 : 0.0;
+    return (y0 == 0 || y0 == T) ? 0.5 : 1.0;
+}
+
+static void shifted(const geom* g, const int x[4], int nu, int d, int out[4])
+{
+    out[0] = x[0]; out[1] = x[1]; out[2] = x[2]; out[3] = x[3];
+    if (nu == 0) out[0] += d;
+    else out[nu] = (out[nu] + d + g->L) % g->L;
+}
+
+/*
+ * Force of the gauge action for the HMC trajectory around Alg. 2 (the steps
+ * either side of the fermion force): F^a_mu(x) = dS_g / d omega^a for
+ * U_mu(x) -> exp(i omega^a T^a) U_mu(x).  Every plaquette through U_mu(x),
+ * traced from that link, is Re tr(U_mu(x) A) with A its staple, and
+ * d/d omega Re tr(e^{i omega T^a} U A) = -Im tr(T^a U A) at omega = 0, so
+ *   F^a_mu(x) = (beta / 3) sum_staples w(p) Im tr(T^a U_mu(x) A_p),
+ *   up staple   A = U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag        (base x),
+ *   down staple A = U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)   (base x-nu).
+ * Dynamic links: U_0(x) with x0 = 0..T-1 and U_k(x) with x0 = 1..T-1; the
+ * spatial boundary links at x0 = 0, T are fixed and get F = 0.
+ */
+int sfo_gauge_force(int L, int T, double beta, const double* Ud, double* F)
+{
+    if (check_args(L, T)) return -1;
+    init_tables();
+    geom g = make_geom(L, T, 0.0, 0);
+    const cplx* U = (const cplx*)Ud;
+    memset(F, 0, sizeof(double) * g.Vg * 4 * 8);
+#pragma omp parallel for schedule(static)
+    for (long gi = 0; gi < g.Vg; ++gi) {
+        int x[4];
+        gcoords(&g, gi, x);
+        for (int mu = 0; mu < 4; ++mu) {
+            const int dynamic = (mu == 0) ? (x[0] <= T - 1) : (x[0] >= 1 && x[0] <= T - 1);
+            if (!dynamic) continue;
+            cplx S[9] = {0};  /* sum of weighted staples */
+            for (int nu = 0; nu < 4; ++nu) {
+                if (nu == mu) continue;
+                int xm[4], xn[4], xmn[4], xnd[4];
+                shifted(&g, x, mu, +1, xm);
+                /* up */
+                const double wu = plaq_weight(T, x[0], mu, nu);
+                if (wu != 0.0) {
+                    shifted(&g, x, nu, +1, xn);
+                    cplx B[9], C[9], D[9], E[9];
+                    mat_dag(link(&g, U, xn, mu), B);
+                    mat_mul(link(&g, U, xm, nu), B, C);
+                    mat_dag(link(&g, U, x, nu), D);
+                    mat_mul(C, D, E);
+                    for (int k = 0; k < 9; ++k) S[k] += wu * E[k];
+                }
+                /* down */
+                shifted(&g, x, nu, -1, xnd);
+                const double wd = plaq_weight(T, xnd[0], mu, nu);
+                if (wd != 0.0) {
+                    shifted(&g, xm, nu, -1, xmn);
+                    cplx B[9], C[9], D[9];
+                    mat_dag(link(&g, U, xmn, nu), B);
+                    mat_dag(link(&g, U, xnd, mu), C);
+                    mat_mul(B, C, D);
+                    cplx E[9];
+                    mat_mul(D, link(&g, U, xnd, nu), E);
+                    for (int k = 0; k < 9; ++k) S[k] += wd * E[k];
+                }
+            }
+            cplx W[9];
+            mat_mul(link(&g, U, x, mu), S, W);
+            for (int a = 0; a < 8; ++a) {
+                cplx tr = 0;  /* tr(lambda^a W) */
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) tr += GELL[a][r][c] * W[c * 3 + r];
+                F[(gi * 4 + mu) * 8 + a] = beta / 6.0 * cimag(tr);
+            }
+        }
+    }
+    return 0;
 }
 
 int sfo_num_threads(void)

@@ -11,6 +11,7 @@ tensors (host or CUDA), complex128 in the canonical layouts of the header:
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from dataclasses import dataclass, field
 from typing import List, Optional, Sequence
@@ -55,6 +56,20 @@ class SolveInfo(ctypes.Structure):
                     seconds=self.seconds, kernel_launches=self.kernel_launches)
 
 
+class MdInfo(ctypes.Structure):
+    _fields_ = [
+        ("kinetic", ctypes.c_double * 2), ("s_gauge", ctypes.c_double * 2),
+        ("s_fermion", ctypes.c_double * 2), ("dH", ctypes.c_double),
+        ("force_evals", ctypes.c_int), ("inner_iters", ctypes.c_int),
+        ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+    ]
+
+    def as_dict(self) -> dict:
+        return dict(kinetic=list(self.kinetic), s_gauge=list(self.s_gauge), s_fermion=list(self.s_fermion),
+                    dH=self.dH, force_evals=self.force_evals, inner_iters=self.inner_iters,
+                    seconds=self.seconds, kernel_launches=self.kernel_launches)
+
+
 _lib = None
 
 
@@ -78,6 +93,10 @@ def lib() -> ctypes.CDLL:
         L.fermion_force.argtypes = [vp, i, vp, vp, vp, vp, d]
         L.md_force_step.argtypes = [vp, i, i, vp, vp, vp, vp, vp, d, d, i, ctypes.POINTER(SolveInfo)]
         L.plaquette_action.argtypes = [vp, ctypes.POINTER(d)]
+        L.gauge_force.argtypes = [vp, vp, vp, d]
+        L.sf_lattice_update_links.argtypes = [vp, vp, d]
+        L.sf_lattice_get_links.argtypes = [vp, vp]
+        L.sf_md_trajectory.argtypes = [vp, i, i, vp, vp, i, d, d, i, ctypes.POINTER(MdInfo)]
         L.plaquette_action_noalloc.argtypes = [i, i, d, vp, vp, i, vp]
         L.plaquette_action_noalloc.restype = ctypes.c_int
         L.sf_cnn_num_params.argtypes = [i]
@@ -276,6 +295,70 @@ def plaquette_action(lat: Lattice) -> float:
     S = ctypes.c_double()
     _check(lib().plaquette_action(lat.handle, ctypes.byref(S)))
     return S.value
+
+
+# ---------------------------------------------------------------- HMC trajectory
+
+def _mom_bytes(lat: Lattice) -> int:
+    return (lat.T + 1) * lat.L ** 3 * 4 * 8 * 8
+
+
+def gauge_force(lat: Lattice, F=None, mom=None, eps: float = 0.0) -> None:
+    """Force of the plaquette action (F and / or mom -= eps F), zero on the
+    fixed boundary links."""
+    if F is not None:
+        _check_size(F, _mom_bytes(lat), "F")
+    if mom is not None:
+        _check_size(mom, _mom_bytes(lat), "mom")
+    _check(lib().gauge_force(lat.handle, _ptr(F), _ptr(mom), eps))
+
+
+def update_links(lat: Lattice, mom, dt: float) -> None:
+    """U <- exp(i dt P) U on the dynamic links (P = P^a T^a from mom)."""
+    _check_size(mom, _mom_bytes(lat), "mom")
+    _check(lib().sf_lattice_update_links(lat.handle, _ptr(mom), dt))
+
+
+def get_links(lat: Lattice, out) -> None:
+    """Copy the lattice's current FP64 links into out (canonical layout)."""
+    _check_size(out, (lat.T + 1) * lat.L ** 3 * 4 * 18 * 8, "links")
+    _check(lib().sf_lattice_get_links(lat.handle, _ptr(out)))
+
+
+def md_trajectory(lat: Lattice, algo: str, phi, mom, nsteps: int, dt: float, tol: float = 1e-10,
+                  maxiter: int = 10000, allow_noconv: bool = False) -> dict:
+    """One leapfrog MD trajectory (gauge + fermion force for the pseudo-fermions
+    phi); moves the lattice's links and mom in place; returns the Hamiltonian
+    parts at both ends and dH."""
+    nrhs = _nrhs_of(phi, lat.Vh * 24 * 8)
+    _check_size(mom, _mom_bytes(lat), "mom")
+    info = MdInfo()
+    rc = lib().sf_md_trajectory(lat.handle, ALGOS[algo], nrhs, _ptr(phi), _ptr(mom), nsteps, dt, tol, maxiter,
+                                ctypes.byref(info))
+    _check(rc, allow_noconv)
+    d = info.as_dict()
+    d["status"] = STATUS[rc]
+    return d
+
+
+def hmc_trajectory(lat: Lattice, algo: str, eta, mom, uniform: float, nsteps: int, dt: float,
+                   tol: float = 1e-10, maxiter: int = 10000) -> dict:
+    """One HMC trajectory with the caller's random numbers: pseudo-fermions
+    phi = Dhat eta from the Gaussian even-site fields eta (so S_f = |eta|^2 at
+    the start), an MD trajectory from the momenta mom, and the Metropolis
+    test: accepted if uniform < exp(-dH), else the links are restored.
+    Returns the md_trajectory dict with "accepted"."""
+    import torch
+
+    phi = torch.empty_like(eta)
+    wilson_apply_block(lat, "dhat", "fp64", eta, phi)
+    old = torch.empty((lat.T + 1) * lat.L ** 3 * 4 * 18, dtype=torch.float64, device=eta.device)
+    get_links(lat, old)
+    d = md_trajectory(lat, algo, phi, mom, nsteps, dt, tol, maxiter)
+    d["accepted"] = bool(uniform < math.exp(min(0.0, -d["dH"])))
+    if not d["accepted"]:
+        lat.set_links(old)
+    return d
 
 
 class Batch:

@@ -1827,6 +1827,163 @@ sf_status plaquette_action(sf_lattice* lat, double* S) {
     });
 }
 
+// ---------------------------------------------------------------- HMC trajectory
+namespace {
+size_t mom_bytes(const sf_lattice* lat) { return (size_t)(lat->T + 1) * lat->L * lat->L * lat->L * 4 * 8 * sizeof(double); }
+
+// rebuild the prepared link copies from the canonical links
+void prepare_links(sf_lattice* lat) {
+    const LatDev g = lat->base_desc();
+    CK(launch_link_prep(g, lat->canon.as<double>(), lat->stream));
+}
+
+// scale * sum of squares of n doubles (device) -> host
+double sumsq(sf_lattice* lat, long long n, const double* x, double scale) {
+    double* base = reinterpret_cast<double*>(lat->scratch.as<char>() + 4096 + 1024 * sizeof(double));
+    CK(launch_sumsq(n, x, scale, base, base + 512, lat->stream));
+    double h = 0;
+    CK(cudaMemcpyAsync(&h, base + 512, sizeof h, cudaMemcpyDeviceToHost, lat->stream));
+    CK(cudaStreamSynchronize(lat->stream));
+    return h;
+}
+}  // namespace
+
+sf_status gauge_force(sf_lattice* lat, double* F, double* mom, double eps) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr, "lattice is NULL");
+        REQUIRE(F != nullptr || mom != nullptr, "F and mom are both NULL");
+        CK(cudaSetDevice(lat->device));
+        cudaStream_t s = lat->stream;
+        const size_t fb = mom_bytes(lat);
+        DevMem fs, ms;
+        double* dF = nullptr;
+        if (F) dF = is_device_ptr(F) ? F : (fs.ensure(fb), fs.as<double>());
+        double* dM = nullptr;
+        if (mom) {
+            if (is_device_ptr(mom)) {
+                dM = mom;
+            } else {
+                ms.ensure(fb);
+                CK(cudaMemcpyAsync(ms.p, mom, fb, cudaMemcpyHostToDevice, s));
+                dM = ms.as<double>();
+            }
+        }
+        CK(launch_gauge_force(lat->L, lat->T, lat->beta, lat->canon.as<double>(), dF, dM, eps, s));
+        if (F && dF != F) CK(cudaMemcpyAsync(F, dF, fb, cudaMemcpyDeviceToHost, s));
+        if (mom && dM != mom) CK(cudaMemcpyAsync(mom, dM, fb, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    });
+}
+
+sf_status sf_lattice_update_links(sf_lattice* lat, const double* mom, double dt) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr && mom != nullptr, "NULL argument");
+        CK(cudaSetDevice(lat->device));
+        DevMem ms;
+        const double* dM = mom;
+        if (!is_device_ptr(mom)) {
+            ms.ensure(mom_bytes(lat));
+            CK(cudaMemcpyAsync(ms.p, mom, mom_bytes(lat), cudaMemcpyHostToDevice, lat->stream));
+            dM = ms.as<double>();
+        }
+        CK(launch_link_update(lat->L, lat->T, lat->canon.as<double>(), dM, dt, lat->stream));
+        prepare_links(lat);
+        CK(cudaStreamSynchronize(lat->stream));
+    });
+}
+
+sf_status sf_lattice_get_links(sf_lattice* lat, double* links) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr && links != nullptr, "NULL argument");
+        CK(cudaSetDevice(lat->device));
+        CK(cudaMemcpyAsync(links, lat->canon.p, lat->links_bytes(), cudaMemcpyDefault, lat->stream));
+        CK(cudaStreamSynchronize(lat->stream));
+    });
+}
+
+sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom, int nsteps,
+                           double dt, double tol, int maxiter, sf_md_info* info) {
+    bool noconv = false;
+    sf_status st = guarded([&] {
+        const auto t0 = std::chrono::steady_clock::now();
+        REQUIRE(lat != nullptr && phi != nullptr && mom != nullptr, "NULL argument");
+        REQUIRE(nsteps >= 1, "nsteps must be >= 1");
+        REQUIRE(dt > 0.0, "dt must be positive");
+        check_nrhs(nrhs);
+        (void)algo_index(algo);
+        CK(cudaSetDevice(lat->device));
+        cudaStream_t s = lat->stream;
+        const size_t fb = mom_bytes(lat);
+        const size_t xb = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
+        DevMem ms, ps, xs, ys;
+        double* dM = mom;
+        if (!is_device_ptr(mom)) {
+            ms.ensure(fb);
+            CK(cudaMemcpyAsync(ms.p, mom, fb, cudaMemcpyHostToDevice, s));
+            dM = ms.as<double>();
+        }
+        const double* dP = phi;
+        if (!is_device_ptr(phi)) {
+            ps.ensure(xb);
+            CK(cudaMemcpyAsync(ps.p, phi, xb, cudaMemcpyHostToDevice, s));
+            dP = ps.as<double>();
+        }
+        xs.ensure(xb);
+        ys.ensure(xb);
+        long long launches = 0;
+        int inner = 0, evals = 0;
+        CK(launch_mom_fix(lat->L, lat->T, dM, s));
+        const long long nmom = (long long)(fb / sizeof(double));
+        // P -= e (F_gauge + F_fermion)(U); returns S_f(U) = sum |X|^2
+        auto kick = [&](double e) {
+            CK(launch_gauge_force(lat->L, lat->T, lat->beta, lat->canon.as<double>(), nullptr, dM, e, s));
+            sf_solve_info fi;
+            const sf_status r = md_force_step(lat, algo, nrhs, dP, xs.as<double>(), ys.as<double>(), nullptr, dM, e,
+                                              tol, maxiter, &fi);
+            if (r == SF_ENOCONV) noconv = true;
+            else if (r != SF_OK) throw SfError{r, g_err};
+            launches += 1 + fi.kernel_launches;
+            inner += fi.iters_inner + fi.iters_inner_y;
+            ++evals;
+            return sumsq(lat, (long long)(xb / sizeof(double)), xs.as<double>(), 1.0);
+        };
+        auto gauge_action = [&](double* S) {
+            const sf_status r = plaquette_action(lat, S);
+            if (r != SF_OK) throw SfError{r, g_err};
+        };
+        sf_md_info out;
+        memset(&out, 0, sizeof out);
+        out.kinetic[0] = sumsq(lat, nmom, dM, 0.5);
+        gauge_action(&out.s_gauge[0]);
+        out.s_fermion[0] = kick(0.5 * dt);
+        double sf_end = out.s_fermion[0];
+        for (int k = 0; k < nsteps; ++k) {
+            CK(launch_link_update(lat->L, lat->T, lat->canon.as<double>(), dM, dt, s));
+            prepare_links(lat);
+            launches += 2;
+            sf_end = kick(k == nsteps - 1 ? 0.5 * dt : dt);
+        }
+        out.kinetic[1] = sumsq(lat, nmom, dM, 0.5);
+        gauge_action(&out.s_gauge[1]);
+        out.s_fermion[1] = sf_end;
+        out.dH = (out.kinetic[1] - out.kinetic[0]) + (out.s_gauge[1] - out.s_gauge[0]) +
+                 (out.s_fermion[1] - out.s_fermion[0]);
+        out.force_evals = evals;
+        out.inner_iters = inner;
+        launches += 5 + 2 * 2 + 2;
+        if (dM != mom) CK(cudaMemcpyAsync(mom, dM, fb, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        out.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        out.kernel_launches = launches;
+        if (info) *info = out;
+    });
+    if (st == SF_OK && noconv) {
+        g_err = "a solve of the trajectory stopped above tolerance";
+        return SF_ENOCONV;
+    }
+    return st;
+}
+
 // ---------------------------------------------------------------- batches
 }  // extern "C"
 

@@ -167,6 +167,15 @@ cudaError_t launch_gamma5_64(long long total_elems, int Vpad, FieldPtr in, Field
 // (device, out[j * 2S + 2 i + (0, 1)], S = 8 for nrhs <= 8 else 16); partials
 // holds nrhs * 2S * nblocks doubles
 cudaError_t launch_gram64(const LaunchCfg&, FieldPtr a, FieldPtr b, double* partials, double* out, cudaStream_t);
+// HMC trajectory (hmc.cu), canonical links and [(T+1) L^3][4][8] momenta:
+// gauge force (F and / or mom -= eps F), U <- exp(i dt P) U on the dynamic
+// links, zero momenta on the fixed boundary links, and scale * sum x_i^2
+// (part: 304 doubles of scratch)
+cudaError_t launch_gauge_force(int L, int T, double beta, const double* canon, double* F, double* mom, double eps,
+                               cudaStream_t);
+cudaError_t launch_link_update(int L, int T, double* canon, const double* mom, double dt, cudaStream_t);
+cudaError_t launch_mom_fix(int L, int T, double* mom, cudaStream_t);
+cudaError_t launch_sumsq(long long n, const double* x, double scale, double* part, double* out, cudaStream_t);
 // y_j += sum_i x_i coef[i * nrhs + j] (coef on the device; x, y distinct)
 cudaError_t launch_block_axpy64(const LaunchCfg&, FieldPtr x, const double2* coef, FieldPtr y, cudaStream_t);
 
