@@ -161,6 +161,10 @@ def run_ours(args, rank, world, local_rank):
     mom_d = torch.zeros(fshape, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, U_d, device=local_rank)
+    # the precision of the inner solve (its hop is the kernel the roofline reports)
+    prec = "fp32" if args.algo in ("mixed_dc", "cg_normal") else ("fp16" if args.algo == "mixed_dc_half" else "fp64")
+    if args.solve_tiling:  # fixed inner-solve tiling instead of the autotuner's (for reproducible profiles)
+        lat.set_tuning(prec, *args.solve_tiling)
     eps_md = 0.01
 
     def step(Ub, ph, X, Y, F, mom):
@@ -231,7 +235,6 @@ def run_ours(args, rank, world, local_rank):
 
     # ---------------- roofline of the dominant kernel: the FP32 dslash (hop)
     peak, peak_kind = _peaks()
-    prec = "fp32" if args.algo in ("mixed_dc", "cg_normal") else ("fp16" if args.algo == "mixed_dc_half" else "fp64")
     TS, NR, PIPE = lat.get_tuning(prec, nrhs)
     Vh = lt.Vh
     site_bytes = {"fp32": nrhs * 96 * 2 + 8 * 48, "fp16": nrhs * 52 * 2 + 8 * 24,
@@ -631,6 +634,8 @@ def main():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-hmc", action="store_true")
+    ap.add_argument("--solve-tiling", type=int, nargs=3, default=None, metavar=("TS", "NR", "PIPE"),
+                    help="fix the inner solve's tiling of the timed step instead of autotuning it")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-train-fields", type=int, default=8)
     ap.add_argument("--learned-epochs", type=int, default=15)

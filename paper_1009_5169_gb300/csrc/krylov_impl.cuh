@@ -159,7 +159,7 @@ enum FinMode {
     FIN_INIT = 3,  // inner-solve start from |b|^2
     FIN_NORM = 4,  // out[i] = sum
     FIN_DOT = 5,   // ((double2*) out)[i] = (re, im)
-    FIN_INIT_CG = 7,   // CG start: gamma = |b|^2, iters = 0 (k_cg_step's first step), active, target2
+    FIN_INIT_CG = 7,   // CG start: gamma = |b|^2, iters = 0 (k_cg_tail's first step), active, target2
 };
 constexpr int FIN_THREADS = 512;
 
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(KBH<PH, NR, PIPE>::MAXT, KBH<PH, NR, PIPE>::MI
     }
     if (RED == RED_NONE) return;
     if (RED == RED_CG && blockIdx.x == 0) {
-        // start of a CG step (k_cg_step reads these copies while it writes the state)
+        // start of a CG step (k_cg_tail reads these copies while it writes the state)
         const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
         for (int i = tid; i < nlat * nrhs; i += nt) {
             KState& k = ctx.st[i];
@@ -447,23 +447,27 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_s_update
 }
 
 // One CG step on A = Dhat Dhat^dag in the single-reduction form of
-// Chronopoulos and Gear (1989): both inner products of a step come from one
-// pass.  From the lattice sums gamma = |r|^2 and delta = <r, A r> =
-// |Dhat^dag r|^2 of the partials the RED_CG tail wrote for this r (w = A r),
+// Chronopoulos and Gear (1989), fused into the second D-hat tail of the
+// step: both inner products of a step come from one pass.  From the lattice
+// sums gamma = |r|^2 and delta = <r, A r> = |Dhat^dag r|^2 of the partials
+// the RED_CG tail wrote for this r,
 //   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev)
-//   (beta = 0 and alpha = gamma / delta at the first step),
-//   p = r + beta p,  s = w + beta s  (s = A p),  x += alpha p,  r -= alpha s.
-// A rhs stops, before its update, when gamma <= target2, on breakdown
-// (gamma or the denominator not positive), and after maxiter steps.  Every
-// block sums its lattice's partials itself in a fixed order, so all blocks
-// take the same decisions; the lattice's first block records the step in
-// KState.  What the step reads of KState (*_prev, target2, maxiter) no block
-// of this launch writes.  alpha and beta are formed in double (the
-// denominator is a difference) and applied in the vector precision.
-template <typename PV, int NR>
-__global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_cg_step(const LatDev* __restrict__ lats, int nlat, int nrhs,
-                                                  Field<PV> x, Field<PV> r, Field<PV> p, Field<PV> s,
-                                                  CField<PV> w, SolverCtx ctx) {
+//   (beta = 0 and alpha = gamma / delta at the first step);
+// then at every site w = A r = t - kappa^2 H_eo (H_oe t) (t = Dhat^dag r from
+// that tail, hin = H_oe t), and
+//   p = r + beta p,  s = w + beta s  (s = A p),  x += alpha p,  r -= alpha s,
+// so w is never stored.  A rhs stops, before its update, when gamma <=
+// target2, on breakdown (gamma or the denominator not positive), and after
+// maxiter steps.  Every block sums its lattice's partials itself in a fixed
+// order, so all blocks take the same decisions; the lattice's first block
+// records the step in KState.  What the step reads of KState (*_prev,
+// target2, maxiter) no block of this launch writes.  alpha and beta are
+// formed in double (the denominator is a difference) and applied in the
+// vector precision.
+template <typename PV, int NR, bool PIPE>
+__global__ void __launch_bounds__(KBH<PV, NR, PIPE>::MAXT, KBH<PV, NR, PIPE>::MINB) k_cg_tail(
+    const LatDev* __restrict__ lats, int nlat, int nrhs, CField<PV> hin, CField<PV> t, Field<PV> x, Field<PV> r,
+    Field<PV> p, Field<PV> s, SolverCtx ctx) {
     pdl_enter();
     using RV = typename PV::real;
     using A = typename AccOf<RV>::T;
@@ -525,49 +529,58 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_cg_step(
         any = any || md[j] != 0;
     }
     if (!any) return;
+    const RV cv = (RV)(-g.kappa * g.kappa);
     for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
         const int cb = tile_cb(g, tile, threadIdx.x);
         if (cb < 0) continue;
+        const SiteX site = decode_site(g, cb, 0);
+        cpx<RV> acc[NR][4][3];
+        hop_any<PV, NR, false, PIPE>(g, site, cb, 0, hin, r0, nval, acc);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (!md[j]) continue;
             const long long vb = vbase<PV>(g, r0 + j), sb = sbase(g, r0 + j);
             const bool later = (md[j] == 2);
-            // in three stages (p; x; s and r) to bound the live registers
-            cpx<RV> ra[4][3], ta[4][3], ua[4][3];
-            load_spinor<PV, RV>(CField<PV>{r.v, r.scale}, vb, g.Vpad, cb, sb, ra);
-            if (later) {
-                load_spinor<PV, RV>(CField<PV>{p.v, p.scale}, vb, g.Vpad, cb, sb, ta);
-#pragma unroll
-                for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) ta[sp][c] = ra[sp][c] + be[j] * ta[sp][c];
-            } else {
-#pragma unroll
-                for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) ta[sp][c] = ra[sp][c];
-            }
-            store_spinor<PV, RV>(p, vb, g.Vpad, cb, sb, ta);
-            load_spinor<PV, RV>(CField<PV>{x.v, x.scale}, vb, g.Vpad, cb, sb, ua);
+            // in stages (s; p; x; r) to bound the live registers
+            cpx<RV> sa[4][3], ra[4][3], ua[4][3];
+            load_spinor<PV, RV>(t, vb, g.Vpad, cb, sb, sa);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) ua[sp][c] = ua[sp][c] + al[j] * ta[sp][c];
-            store_spinor<PV, RV>(x, vb, g.Vpad, cb, sb, ua);
-            load_spinor<PV, RV>(w, vb, g.Vpad, cb, sb, ta);
-            if (later) {
+                for (int c = 0; c < 3; ++c)
+                    sa[sp][c] = cpx<RV>{sa[sp][c].re + cv * acc[j][sp][c].re, sa[sp][c].im + cv * acc[j][sp][c].im};
+            if (later) {  // s = w + beta s
                 load_spinor<PV, RV>(CField<PV>{s.v, s.scale}, vb, g.Vpad, cb, sb, ua);
 #pragma unroll
                 for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) ta[sp][c] = ta[sp][c] + be[j] * ua[sp][c];
+                    for (int c = 0; c < 3; ++c) sa[sp][c] = sa[sp][c] + be[j] * ua[sp][c];
             }
-            store_spinor<PV, RV>(s, vb, g.Vpad, cb, sb, ta);
+            store_spinor<PV, RV>(s, vb, g.Vpad, cb, sb, sa);
+            load_spinor<PV, RV>(CField<PV>{r.v, r.scale}, vb, g.Vpad, cb, sb, ra);
+            if (later) {  // p = r + beta p
+                load_spinor<PV, RV>(CField<PV>{p.v, p.scale}, vb, g.Vpad, cb, sb, ua);
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ua[sp][c] = ra[sp][c] + be[j] * ua[sp][c];
+            } else {
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ua[sp][c] = ra[sp][c];
+            }
+            store_spinor<PV, RV>(p, vb, g.Vpad, cb, sb, ua);
+            cpx<RV> xa[4][3];
+            load_spinor<PV, RV>(CField<PV>{x.v, x.scale}, vb, g.Vpad, cb, sb, xa);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) ra[sp][c] = ra[sp][c] - al[j] * ta[sp][c];
+                for (int c = 0; c < 3; ++c) {
+                    xa[sp][c] = xa[sp][c] + al[j] * ua[sp][c];
+                    ra[sp][c] = ra[sp][c] - al[j] * sa[sp][c];
+                }
+            store_spinor<PV, RV>(x, vb, g.Vpad, cb, sb, xa);
             store_spinor<PV, RV>(r, vb, g.Vpad, cb, sb, ra);
         }
     }
@@ -923,31 +936,37 @@ struct OpsImpl {
     static int iteration_kernels(const LaunchCfg&) { return 10; }
 
     // ---- one CG step on A = Dhat Dhat^dag (Hermitian, positive) for every
-    // active rhs, in the single-reduction form (k_cg_step):
+    // active rhs, in the single-reduction form (k_cg_tail):
     //   tmp = H^dag r; t = Dhat^dag r with |r|^2, |t|^2 = <r, A r> (opens the
-    //   step, sets the loop condition); tmp = H t; w = Dhat t (in v);
-    //   k_cg_step (alpha, beta; p, s, x, r).  5 kernels.
+    //   step, sets the loop condition); tmp = H t; k_cg_tail (alpha, beta,
+    //   w = Dhat t at each site, then p, s, x, r).  4 kernels.
     static cudaError_t iterate_cg(const LaunchCfg& c, bool, const IterFields& f, const SolverCtx* ctx,
                                   cudaStream_t st) {
         const FieldPtr none{nullptr, nullptr};
         const bool copy = !std::is_same<PV, PH>::value;
         if (copy) return cudaErrorInvalidValue;  // CG runs with FP32 (or FP64) hop operands
+        if (c.pipe && !pipe_ok(c)) return cudaErrorInvalidValue;
         cudaError_t e;
         if ((e = hop(c, 1, true, f.r, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
         if ((e = tail(c, 0, true, RED_CG, f.tmp, f.r, none, f.t, none, 1.0, -1.0, 2, ctx, nullptr, st)) !=
             cudaSuccess)
             return e;
         if ((e = hop(c, 1, false, f.t, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
-        if ((e = tail(c, 0, false, RED_NONE, f.tmp, f.t, none, f.v, none, 1.0, -1.0, 2, ctx, nullptr, st)) !=
-            cudaSuccess)
-            return e;
         SF_NR_SWITCH(c.NR, {
-            launch_pdl(k_cg_step<PV, NR_>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
-                       wf<PV>(f.x), wf<PV>(f.r), wf<PV>(f.p), wf<PV>(f.s), cf<PV>(f.v), *ctx);
+            if constexpr (NR_ <= 2 && !std::is_same<PH, P64>::value) {
+                if (c.pipe) {
+                    launch_pdl(k_cg_tail<PV, NR_, true>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat,
+                               c.nrhs, cf<PV>(f.tmp), cf<PV>(f.t), wf<PV>(f.x), wf<PV>(f.r), wf<PV>(f.p),
+                               wf<PV>(f.s), *ctx);
+                    break;
+                }
+            }
+            launch_pdl(k_cg_tail<PV, NR_, false>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
+                       cf<PV>(f.tmp), cf<PV>(f.t), wf<PV>(f.x), wf<PV>(f.r), wf<PV>(f.p), wf<PV>(f.s), *ctx);
         });
         return cudaGetLastError();
     }
-    static int iteration_kernels_cg(const LaunchCfg&) { return 5; }
+    static int iteration_kernels_cg(const LaunchCfg&) { return 4; }
 
     static cudaError_t init(const LaunchCfg& c, FieldPtr r64, FieldPtr x, FieldPtr r, FieldPtr r0, FieldPtr p,
                             FieldPtr ph, const SolverCtx* ctx, int maxiter, cudaStream_t st) {
