@@ -207,12 +207,15 @@ struct sf_lattice {
 // neighbours (the next tiles of the same block) a step later, so they come
 // from L2 (at 32^4, 8 blocks per SM out of phase with the columns read each
 // input spinor about 2.1 times from DRAM; in phase, 1.2 times).  nseg
-// segments per column give about 12 blocks per SM (measured best at 16^4 to
-// 32^4 among 4, 8, 12); small lattices get one tile per block.
+// segments per column give about 36 blocks per SM over the launch, several
+// waves of the 4 resident 160-thread blocks, so the last partial wave is a
+// small part of the launch (32^4 FP32 hop: 244 us at 12 per SM, 2.5 waves;
+// 227-231 us at 36; 16^4 and 24^4 unchanged); small lattices get one tile
+// per block.
 inline int blocks_for(int L3h, int T, int TS, int sm_count) {
     const int ncol = (L3h + TS - 1) / TS;
     const int ntiles = ncol * (T - 1);
-    const int nseg = std::max(1, std::min(T - 1, (12 * sm_count) / ncol));
+    const int nseg = std::max(1, std::min(T - 1, (36 * sm_count) / ncol));
     return std::min(ntiles, ncol * nseg);
 }
 
