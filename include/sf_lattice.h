@@ -101,7 +101,7 @@ typedef enum {
        learned network attached with sf_lattice_set_preconditioner; the FP64
        true residual judges it, and FP32-inner BiCGStab under FP64 defect
        correction continues from its iterate if it stops above tol.  One
-       lattice only (not batches). */
+       lattice only (not batches), nrhs <= 8 (as Gl- and Bl-BiCGStab). */
     SF_SOLVE_FGCR_CNN = 3,
     /* the same FGCR with the identity as preconditioner (the comparison
        without the network) */
@@ -157,8 +157,8 @@ sf_status sf_lattice_set_links(sf_lattice* lat, const double* links);
 /* Fix the kernel tiling for one precision instead of autotuning it:
  * TS sites per tile (32, 64 or 128) and NR right-hand sides per thread
  * (1, 2, 3 or 5; FP64: 1 or 2).  A block holds TS * ceil(nrhs / NR) threads,
- * at most 256 (FP64, NR = 1), 128 (FP64, NR = 2), 320 / 384 / 256 (FP32 and
- * FP16 with NR = 1 / 2 / 3 or 5): checked when a solve or apply uses the
+ * at most 256 (FP64), 320 / 384 / 256 (FP32 and FP16 with NR = 1 / 2 / 3 or
+ * 5): checked when a solve or apply uses the
  * tiling, SF_EINVAL beyond.  pipe = 1 selects the pipelined hop (operands of
  * the next hops loaded while the current one is applied; FP32 / FP16 only,
  * NR = 1 or 2, at most 256 threads), pipe = 0 the plain one.  TS = 0

@@ -232,7 +232,7 @@ inline bool tiling_ok(int ci, int TS, int NR, int nrhs, int pipe = 0) {
     }
     if (pipe) return false;
     if (NR != 1 && NR != 2) return false;
-    return threads <= (NR == 1 ? 256 : 128);
+    return threads <= 256;
 }
 
 struct GraphEntry {
@@ -717,6 +717,7 @@ void Workspace::autotune(int ci) {
             for (int TS : tss)
                 if (tiling_ok(ci, TS, NR, nrhs, pipe)) cands.push_back(Cand{TS, NR, pipe, 1e30f});
         }
+    REQUIRE(!cands.empty(), "no tiling of this precision fits the number of right-hand sides");
     const FieldPtr none{nullptr, nullptr};
     for (int round = 0; round < 3; ++round)
         for (Cand& cd : cands) {
@@ -765,6 +766,7 @@ void Workspace::autotune(int ci) {
 // correction continues from its iterate.
 Workspace::Result Workspace::fgcr(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
     REQUIRE(nlat == 1, "FGCR runs on a single lattice");
+    REQUIRE(nrhs <= 8, "FGCR, Gl-BiCGStab and Bl-BiCGStab take up to 8 right-hand sides (one 32-site row per rhs)");
     ensure_cfg(0);
     ensure_cfg(3);
     sf_cnn* cnn = lats[0]->cnn;
@@ -988,6 +990,7 @@ void Workspace::precondition(bool dag, const FieldBuf& in, FieldBuf& out, double
 // calls, inner = FP32 iterations per rhs.
 Workspace::Result Workspace::gl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
     REQUIRE(nlat == 1, "Gl-BiCGStab runs on a single lattice");
+    REQUIRE(nrhs <= 8, "FGCR, Gl-BiCGStab and Bl-BiCGStab take up to 8 right-hand sides (one 32-site row per rhs)");
     ensure_cfg(0);
     ensure_cfg(1);
     ensure_cfg(3);
@@ -1199,6 +1202,7 @@ void Workspace::block_axpy64(const FieldBuf& x, const std::vector<std::complex<d
 // all s columns twice).
 Workspace::Result Workspace::bl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
     REQUIRE(nlat == 1, "Bl-BiCGStab runs on a single lattice");
+    REQUIRE(nrhs <= 8, "FGCR, Gl-BiCGStab and Bl-BiCGStab take up to 8 right-hand sides (one 32-site row per rhs)");
     ensure_cfg(0);
     ensure_cfg(3);
     cudaStream_t s = stream;

@@ -45,7 +45,7 @@ __device__ __forceinline__ long long sbase(const LatDev& g, int rhs) { return g.
 template <typename P, int NR>
 struct KB {
     static constexpr bool F64 = std::is_same<P, P64>::value;
-    static constexpr int MAXT = F64 ? (NR == 1 ? 256 : 128) : (NR == 1 ? 320 : NR == 2 ? 384 : 256);
+    static constexpr int MAXT = F64 ? 256 : (NR == 1 ? 320 : NR == 2 ? 384 : 256);
     static constexpr int MINB = F64 ? 1 : (NR == 1 ? 2 : 1);
 };
 // hop and tail kernels: the pipelined hop's blocks hold at most 256 threads
