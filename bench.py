@@ -223,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_s += time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dev)
     nb = lambda a: a.numel() * a.element_size()
-    h2d = nb(U_h) + nb(phi_h) + nb(X_h) + nb(Y_h) + nb(mom_h)   # links, phi, X and Y into the force, mom
+    h2d = nb(U_h) + nb(phi_h) + nb(mom_h)   # links, phi, mom (md_force_step only writes X, Y, F)
     d2h = nb(X_h) + nb(Y_h) + nb(F_h) + nb(mom_h)
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 

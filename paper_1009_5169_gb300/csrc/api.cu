@@ -166,6 +166,10 @@ struct sf_lattice {
     DevMem canon, u64, u32, u16;
     DevMem scratch;      // plaquette partials + scalars
     DevMem stage_in, stage_out;  // device staging for host arrays
+    DevMem stage_out2;           // a second output staging buffer (md_force_step's Y)
+    DevMem stage_f, stage_m;     // force and momentum staging (host F, mom)
+    cudaStream_t side = nullptr; // device-to-host copies that overlap the compute stream
+    cudaEvent_t side_ev = nullptr;
     int tune_TS[3] = {0, 0, 0}, tune_NR[3] = {0, 0, 0}, tune_pipe[3] = {0, 0, 0};
     struct Workspace* ws = nullptr;  // own solver workspace (created on first use)
     sf_cnn* cnn = nullptr;           // learned preconditioner for SF_SOLVE_FGCR_CNN (not owned)
@@ -1487,6 +1491,11 @@ void sf_lattice_destroy(sf_lattice* lat) {
     if (!lat) return;
     cudaSetDevice(lat->device);
     if (lat->stream) cudaStreamSynchronize(lat->stream);
+    if (lat->side) {
+        cudaStreamSynchronize(lat->side);
+        cudaStreamDestroy(lat->side);
+    }
+    if (lat->side_ev) cudaEventDestroy(lat->side_ev);
     delete lat->ws;
     delete lat;
 }
@@ -1703,27 +1712,24 @@ void force_from_workspace(sf_lattice* lat, Workspace& w, double* F, double* mom,
     const size_t fbytes = (size_t)(lat->T + 1) * lat->L * lat->L * lat->L * 4 * 8 * sizeof(double);
     double* dF = nullptr;
     if (F) {
-        dF = out_device(F, fbytes, lat->stage_out);
+        dF = out_device(F, fbytes, lat->stage_f);
         CK(cudaMemsetAsync(dF, 0, fbytes, s));
     }
     double* dM = nullptr;
-    DevMem mstage;
     if (mom) {
         if (is_device_ptr(mom)) {
             dM = mom;
         } else {
-            mstage.ensure(fbytes);
-            CK(cudaMemcpyAsync(mstage.p, mom, fbytes, cudaMemcpyHostToDevice, s));
-            dM = mstage.as<double>();
+            lat->stage_m.ensure(fbytes);
+            CK(cudaMemcpyAsync(lat->stage_m.p, mom, fbytes, cudaMemcpyHostToDevice, s));
+            dM = lat->stage_m.as<double>();
         }
     }
     CK(launch_force(pl, w.x64.ptr(), w.xo64.ptr(), w.y64.ptr(), w.yo64.ptr(), dF, dM, eps, s));
     w.launches += 1;
-    if (F) finish_out(F, dF, fbytes, s);
-    if (mom && dM != mom) {
-        CK(cudaMemcpyAsync(mom, dM, fbytes, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-    }
+    if (F && dF != F) CK(cudaMemcpyAsync(F, dF, fbytes, cudaMemcpyDeviceToHost, s));
+    if (mom && dM != mom) CK(cudaMemcpyAsync(mom, dM, fbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
 }
 
@@ -1796,16 +1802,28 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         } else {
             rx = run(false, w.phi64, w.x64, w.xo64);
         }
-        double* dX = out_device(X, bytes, lat->stage_out);
-        CK(o.unpack(pl, w.x64.ptr(), dX, s));
-        finish_out(X, dX, bytes, s);
+        // host outputs: X and Y leave on the side stream while the Y solve and
+        // the force run on the compute stream
+        if ((!is_device_ptr(X) || !is_device_ptr(Y)) && !lat->side) {
+            CK(cudaStreamCreateWithFlags(&lat->side, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&lat->side_ev, cudaEventDisableTiming));
+        }
+        auto out_async = [&](double* dst, FieldBuf& f, DevMem& stage) {
+            double* dv = out_device(dst, bytes, stage);
+            CK(o.unpack(pl, f.ptr(), dv, s));
+            if (dv != dst) {
+                CK(cudaEventRecord(lat->side_ev, s));
+                CK(cudaStreamWaitEvent(lat->side, lat->side_ev, 0));
+                CK(cudaMemcpyAsync(dst, dv, bytes, cudaMemcpyDeviceToHost, lat->side));
+            }
+        };
+        out_async(X, w.x64, lat->stage_out);
         if (!normal) ry = run(true, w.x64, w.y64, w.yo64);
-        double* dY = out_device(Y, bytes, lat->stage_out);
-        CK(o.unpack(pl, w.y64.ptr(), dY, s));
-        finish_out(Y, dY, bytes, s);
+        out_async(Y, w.y64, lat->stage_out2);
         w.launches += 2;
         force_from_workspace(lat, w, F, mom, eps);
         CK(cudaStreamSynchronize(s));
+        if (lat->side) CK(cudaStreamSynchronize(lat->side));
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         fill_info(info, rx, &ry, 0, nrhs, secs, w.launches);
         if (!rx.converged || !ry.converged) noconv = true;

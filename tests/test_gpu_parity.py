@@ -219,6 +219,34 @@ def test_md_force_step_matches_separate_calls(sf, algo):
     lat.close()
 
 
+@pytest.mark.parametrize("algo", ["cg_normal", "mixed_dc"])
+def test_md_force_step_host_buffers(sf, algo):
+    """Alg. 2 in one call with host (pageable and pinned) buffers gives bitwise
+    the device-buffer results (the X, Y copies leave on a side stream while
+    the Y solve and the force run)."""
+    L, T, eps, kappa, theta = 6, 7, 0.3, 0.13, 0.5
+    U = inputs.links(L, T, eps, 151)
+    phi = inputs.sources(L, T, 3, 152)
+    lat = sf.Lattice(L, T, theta, kappa, 4.52, torch.from_numpy(U).cuda())
+    fshape = ((T + 1) * L ** 3, 4, 8)
+    pd = torch.from_numpy(phi).cuda()
+    Xd, Yd = torch.empty_like(pd), torch.empty_like(pd)
+    Fd = torch.zeros(fshape, dtype=torch.float64, device="cuda")
+    Md = torch.ones(fshape, dtype=torch.float64, device="cuda")
+    sf.md_force_step(lat, algo, pd, Xd, Yd, Fd, Md, eps=0.2, tol=1e-10, maxiter=3000)
+    for pin in (False, True):
+        ph = torch.from_numpy(phi.copy())
+        Xh, Yh = torch.empty_like(ph), torch.empty_like(ph)
+        Fh = torch.zeros(fshape, dtype=torch.float64)
+        Mh = torch.ones(fshape, dtype=torch.float64)
+        if pin:
+            ph, Xh, Yh, Fh, Mh = (t.pin_memory() for t in (ph, Xh, Yh, Fh, Mh))
+        sf.md_force_step(lat, algo, ph, Xh, Yh, Fh, Mh, eps=0.2, tol=1e-10, maxiter=3000)
+        assert torch.equal(Xh, Xd.cpu()) and torch.equal(Yh, Yd.cpu())
+        assert torch.equal(Fh, Fd.cpu()) and torch.equal(Mh, Md.cpu())
+    lat.close()
+
+
 def test_gl_bicgstab_five_rhs_sf12(sf):
     """The paper's D1 solver (Sec. 3.2): Gl-BiCGStab in FP64 over the block of
     5 pseudo-fermions, preconditioned by FP32 BiCGStab solves; X and Y reach
