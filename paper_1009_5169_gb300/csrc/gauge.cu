@@ -298,12 +298,15 @@ __global__ void __launch_bounds__(128) k_force(const LatDev* __restrict__ lat, i
     const int par = blockIdx.y;
     const CField<P64> xs = par ? xo : xe, ys = par ? yo : ye;
     const CField<P64> xn = par ? xe : xo, yn = par ? ye : yo;
+    const int mu = blockIdx.z;  // one direction per grid layer: four times the threads of one per site
     for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.Vh; cb += gridDim.x * blockDim.x) {
         const SiteX s = decode_site(g, cb, par);
-        force_dir<0>(g, s, cb, par, nrhs, xs, ys, xn, yn, F, mom, eps);
-        force_dir<1>(g, s, cb, par, nrhs, xs, ys, xn, yn, F, mom, eps);
-        force_dir<2>(g, s, cb, par, nrhs, xs, ys, xn, yn, F, mom, eps);
-        force_dir<3>(g, s, cb, par, nrhs, xs, ys, xn, yn, F, mom, eps);
+        switch (mu) {
+            case 0: force_dir<0>(g, s, cb, par, nrhs, xs, ys, xn, yn, F, mom, eps); break;
+            case 1: force_dir<1>(g, s, cb, par, nrhs, xs, ys, xn, yn, F, mom, eps); break;
+            case 2: force_dir<2>(g, s, cb, par, nrhs, xs, ys, xn, yn, F, mom, eps); break;
+            default: force_dir<3>(g, s, cb, par, nrhs, xs, ys, xn, yn, F, mom, eps); break;
+        }
     }
 }
 
@@ -313,7 +316,7 @@ cudaError_t launch_force(const LaunchCfg& c, FieldPtr xe, FieldPtr xo, FieldPtr 
     // grid is sized from the host copy passed through nblocks.
     int blocks = c.nblocks;
     if (blocks < 1) blocks = 1;
-    launch_pdl(k_force, dim3(dim3(blocks, 2)), dim3(128), st, c.lats, c.nrhs, cf<P64>(xe), cf<P64>(xo), cf<P64>(ye), cf<P64>(yo),
+    launch_pdl(k_force, dim3(dim3(blocks, 2, 4)), dim3(128), st, c.lats, c.nrhs, cf<P64>(xe), cf<P64>(xo), cf<P64>(ye), cf<P64>(yo),
                                              F, mom, eps);
     return cudaGetLastError();
 }
