@@ -416,8 +416,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer" if prec == "fp32" else prec,
         "data": "synthetic (seeded SF gauge field exp(i eps H) and Gaussian pseudo-fermions)",
-        "config": {"workload": f"{args.workload}: {lt.L}^3x{lt.T} SF, eps {lt.eps}, kappa {lt.kappa}, "
-                               f"theta {lt.theta}, {nrhs} RHS, tol {tol}, X and Y solves + force",
+        "config": {"workload": _workload_desc(args.workload, lt, nrhs, tol),
                    "algo": args.algo, "l2": "flushed between steps", "parallelism": f"replicas x{world}",
                    "tiling": {"fp64": lat.get_tuning("fp64", nrhs), prec: (TS, NR, PIPE)}},
         "accuracy": {"max_true_rel_resid": resid, "sweeps_x": last["iters_outer"], "inner_iters_x": last["iters_inner"],
@@ -452,6 +451,12 @@ def _oracle_step_estimate(w, U, phi, calib, sample_iters):
     per_iter = (t1 - t0) / max(1, int(it_x[0]) + int(it_y[0]))
     full = w.nrhs * (per_iter * (calib[0] + calib[1]) + (t2 - t1))
     return full, (t2 - t0)
+
+
+def _workload_desc(name, lt, nrhs, tol):
+    """The workload as both arms name it in `config`."""
+    return (f"{name}: {lt.L}^3x{lt.T} SF, eps {lt.eps}, kappa {lt.kappa}, theta {lt.theta}, {nrhs} RHS, "
+            f"tol {tol}, X and Y solves + force")
 
 
 def _oracle_calibrate(w, U, phi):
@@ -505,7 +510,7 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": round(sps, 6), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(est) * 1e3, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": args.workload},
+           "data": "synthetic", "config": {"workload": _workload_desc(args.workload, lt, w.nrhs, w.tol)},
            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": round(sps, 6), "unit": UNIT,
                             "sample": f"per step: 10+10 BiCGStab iterations and one force on one field, scaled by "
                                       f"the calibrated {calib[0]}+{calib[1]} iterations and {w.nrhs} fields"},
