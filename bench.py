@@ -12,8 +12,8 @@ plus the force), summed over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle on the same workload (bounded
-samples scaled to a full step).  Under torchrun every rank runs its own
+--impl reference times the FP64 CPU oracle on the same workload (full
+steps, measured, on the host cores).  Under torchrun every rank runs its own
 replica of the workload (the path has no exchange step); the time is the
 maximum over ranks.
 """
@@ -228,10 +228,26 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---------------- accuracy re-check outside the timed region: solve_block
-    # recomputes both FP64 true residuals (md_force_step with the CG route
-    # reports Y's, the rounding-level |X - Dhat^dag Y|, without recomputing it)
+    # recomputes the FP64 true residual |Phi - Dhat X| / |Phi| of every RHS.
+    # With the normal-equation route X is formed as Dhat^dag Y by the FP64
+    # kernel, so |X - Dhat^dag Y| is zero by construction and Y's accuracy is
+    # that of |Phi - Dhat Dhat^dag Y| = |Phi - Dhat X|; the oracle's own
+    # residuals of the final X and Y (both equations of Alg. 2) are in
+    # cpu_baseline.oracle_check.
     chk = sf.solve_block(lat, args.algo, phi_d, X_d, Y_d, tol=tol, maxiter=args.maxiter)
-    recheck = {"max_true_rel_resid_x": max(chk["true_resid"]), "max_true_rel_resid_y": max(chk["true_resid_y"])}
+    recheck = {"max_true_rel_resid_x": max(chk["true_resid"]),
+               "max_true_rel_resid_y": max(chk["true_resid_y"]),
+               "note": ("cg_normal: X = Dhat^dag Y by construction, so the Y line is |X - Dhat^dag Y| = 0; "
+                        "the oracle's residuals of both are under cpu_baseline.oracle_check")
+               if args.algo == "cg_normal" else "library FP64 recomputation"}
+    host_solution = {"X": X_d.cpu().numpy(), "Y": Y_d.cpu().numpy()}
+
+    # ---------------- the 16^4 kappa 0.134 workload: FP32- and FP16-inner
+    # solves (their per-RHS error against the oracle is measured in the
+    # cpu_baseline leg)
+    acc_cfg = None
+    if not args.no_accuracy_configs and rank == 0:
+        acc_cfg = accuracy_config_solves(args, sf, inputs, dev, local_rank)
 
     # ---------------- roofline of the dominant kernel: the FP32 dslash (hop)
     peak, peak_kind = _peaks()
@@ -383,29 +399,10 @@ def run_ours(args, rank, world, local_rank):
         for bl in blats:
             bl.close()
 
-    # ---------------- one HMC trajectory around the MD step (same lattice and pseudo-fermion count)
+    # ---------------- HMC trajectories around the MD step (same lattice and pseudo-fermion count)
     hmc = None
     if not args.no_hmc and rank == 0:
-        hlat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, U_d, device=local_rank)
-        P0 = torch.from_numpy(inputs.su3_directions(fshape[:2], inputs.SEED_BASE + 501)).to(dev)
-        eta = torch.from_numpy(inputs.sources(lt.L, lt.T, nrhs, inputs.SEED_BASE + 502)).to(dev)
-        hphi = torch.empty_like(eta)
-        sf.wilson_apply_block(hlat, "dhat", "fp64", eta, hphi)
-        nst, dt = 10, 0.02
-        sf.md_trajectory(hlat, args.algo, hphi, P0.clone(), 2, dt, tol=tol, maxiter=args.maxiter)  # warm-up
-        hlat.set_links(U_d)
-        mom_t = P0.clone()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hinfo = sf.md_trajectory(hlat, args.algo, hphi, mom_t, nst, dt, tol=tol, maxiter=args.maxiter)
-        torch.cuda.synchronize()
-        th = time.perf_counter() - t0
-        hmc = {"workload": f"{lt.L}^3x{lt.T} SF, {nrhs} pseudo-fermions phi = Dhat eta, Gaussian momenta, "
-                           f"leapfrog {nst} x dt {dt} (trajectory length {nst * dt:g}), {args.algo} to {tol}",
-               "ms": round(th * 1e3, 2), "force_evals": hinfo["force_evals"],
-               "ms_per_force_eval": round(th * 1e3 / hinfo["force_evals"], 3), "dH": hinfo["dH"],
-               "inner_iters": hinfo["inner_iters"], "kernel_launches": hinfo["kernel_launches"]}
-        hlat.close()
+        hmc = hmc_section(args, sf, inputs, lt, U_d, nrhs, tol, fshape, dev, local_rank)
 
     learned = None
     if not args.no_learned and rank == 0:
@@ -424,10 +421,11 @@ def run_ours(args, rank, world, local_rank):
                      "solve_block_recheck": recheck},
         "roofline": roofline, "dslash_hbm": hbm, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "comparators": comparators, "batched": batched, "hmc_trajectory": hmc, "learned": learned,
+        "accuracy_configs": acc_cfg["summary"] if acc_cfg else None,
     }
     lat.close()
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline(args, host_solution, acc_cfg)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -435,22 +433,17 @@ def run_ours(args, rank, world, local_rank):
 
 
 # --------------------------------------------------------------------- oracle
-def _oracle_step_estimate(w, U, phi, calib, sample_iters):
-    """Time a bounded sample of the oracle on one pseudo-fermion field and
-    scale it to a full 5-field step.  calib holds the oracle's full-solve
-    iteration counts for one field (measured once)."""
+def _oracle_full_step(w, U, phi):
+    """One full step of the FP64 oracle on the workload: X = Dhat^-1 Phi and
+    Y = Dhat^-dag X for every pseudo-fermion field to the workload's true
+    residual (textbook BiCGStab, one field after the other), then the force of
+    Eq. (3).  Returns (seconds, X, Y, info)."""
     import oracle
     lt = w.lattices[0]
     t0 = time.perf_counter()
-    x, it_x, _ = oracle.bicgstab(U, phi[:1], lt.L, lt.T, lt.theta, lt.kappa, tol=w.tol, maxiter=sample_iters)
-    y, it_y, _ = oracle.bicgstab(U, x, lt.L, lt.T, lt.theta, lt.kappa, tol=w.tol, maxiter=sample_iters,
-                                 dagger=True)
-    t1 = time.perf_counter()
-    oracle.force(U, x, y, lt.L, lt.T, lt.theta, lt.kappa)
-    t2 = time.perf_counter()
-    per_iter = (t1 - t0) / max(1, int(it_x[0]) + int(it_y[0]))
-    full = w.nrhs * (per_iter * (calib[0] + calib[1]) + (t2 - t1))
-    return full, (t2 - t0)
+    X, Y, info = oracle.solve_pair(U, phi, lt.L, lt.T, lt.theta, lt.kappa, tol=w.tol, maxiter=20000)
+    oracle.force(U, X, Y, lt.L, lt.T, lt.theta, lt.kappa)
+    return time.perf_counter() - t0, X, Y, info
 
 
 def _workload_desc(name, lt, nrhs, tol):
@@ -459,36 +452,169 @@ def _workload_desc(name, lt, nrhs, tol):
             f"tol {tol}, X and Y solves + force")
 
 
-def _oracle_calibrate(w, U, phi):
-    import oracle
-    lt = w.lattices[0]
-    x, it_x, _ = oracle.bicgstab(U, phi[:1], lt.L, lt.T, lt.theta, lt.kappa, tol=w.tol, maxiter=20000)
-    _, it_y, _ = oracle.bicgstab(U, x, lt.L, lt.T, lt.theta, lt.kappa, tol=w.tol, maxiter=20000, dagger=True)
-    return int(it_x[0]), int(it_y[0])
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
-def cpu_baseline(args, budget_s=20.0):
-    """The FP64 oracle as it stands on the host cores: one full solve pair of
-    one field calibrates the iteration counts; a bounded sample of iterations
-    plus one force gives the time of a 5-field step."""
+def _per_rhs_relerr(a, b):
+    n = a.shape[0]
+    return (np.linalg.norm((a - b).reshape(n, -1), axis=1) / np.linalg.norm(b.reshape(n, -1), axis=1)).tolist()
+
+
+def cpu_baseline(args, host_solution=None, acc_cfg=None):
+    """The FP64 oracle as it stands, timed on the host cores: full steps of
+    the bench workload (every field's X and Y to the workload's residual and
+    the force), once with OpenMP on every core this process may run on and
+    once single-threaded.  The same leg checks the GPU's results with the
+    oracle: its true residuals of the bench step's X and Y, and on the 16^4
+    kappa 0.134 workload every RHS's error of the FP32- and FP16-inner
+    solutions against the oracle's own solutions (solved to 1e-12)."""
     import oracle
     from paper_1009_5169_gb300 import inputs
     w = inputs.workload(args.workload)
     lt = w.lattices[0]
     U = lt.make_links()
     phi = lt.make_sources(w.nrhs)
+    cores = _host_cores()
+    oracle.set_num_threads(cores)
+    t_all, Xo, Yo, info = _oracle_full_step(w, U, phi)
+    out = {"value": round(1.0 / t_all, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"one full step of the workload, measured: {w.nrhs} fields, X and Y by FP64 BiCGStab to "
+                     f"{w.tol} ({int(np.sum(info['iters_x']))}+{int(np.sum(info['iters_y']))} iterations) and "
+                     f"the force, OpenMP on {cores} cores",
+           "seconds_per_step": round(t_all, 3)}
+    if not args.no_cpu_single:
+        oracle.set_num_threads(1)
+        t_one, _, _, _ = _oracle_full_step(w, U, phi)
+        oracle.set_num_threads(cores)
+        out["single_thread"] = {"value": round(1.0 / t_one, 6), "unit": UNIT, "cores": 1,
+                                "seconds_per_step": round(t_one, 3), "sample": "the same full step, one thread"}
+    if host_solution is not None:
+        X, Y = host_solution["X"], host_solution["Y"]
+        rx = oracle.true_residual(U, phi, X, lt.L, lt.T, lt.theta, lt.kappa)
+        ry = oracle.true_residual(U, X, Y, lt.L, lt.T, lt.theta, lt.kappa, dagger=True)
+        out["oracle_check"] = {
+            "what": "the bench step's final X, Y: the oracle's true residuals |Phi - Dhat X|/|Phi| and "
+                    "|X - Dhat^dag Y|/|X| per RHS, and the error against the oracle's X, Y (solved to the same "
+                    "1e-10, so that difference is bounded by both solutions' errors)",
+            "resid_x": [float(v) for v in rx], "resid_y": [float(v) for v in ry],
+            "err_x_vs_oracle_1e-10": _per_rhs_relerr(X, Xo), "err_y_vs_oracle_1e-10": _per_rhs_relerr(Y, Yo)}
+    if acc_cfg is not None:
+        out["oracle_check_sf16"] = _oracle_check_sf16(acc_cfg, cores)
+    return out
+
+
+def _oracle_check_sf16(acc_cfg, cores):
+    """The oracle's X, Y of the 16^4 kappa 0.134 workload at 1e-12, and the
+    GPU solutions' per-RHS errors against them and oracle residuals."""
+    import oracle
+    w, lt, U, phi = acc_cfg["workload"]
     t0 = time.perf_counter()
-    calib = _oracle_calibrate(w, U, phi)
-    tcal = time.perf_counter() - t0
-    est, used = _oracle_step_estimate(w, U, phi, calib, 40)
-    return {"value": round(1.0 / est, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"one of the {w.nrhs} fields: full X and Y solves (calibration, {tcal:.1f}s, "
-                      f"{calib[0]}+{calib[1]} BiCGStab iterations) and 40+40 iterations plus one force "
-                      f"({used:.1f}s), scaled to {w.nrhs} fields",
-            "seconds_per_step": round(est, 3)}
+    Xo, Yo, info = oracle.solve_pair(U, phi, lt.L, lt.T, lt.theta, lt.kappa, tol=1e-12, maxiter=20000)
+    t_or = time.perf_counter() - t0
+    res = {"workload": acc_cfg["summary"]["workload"],
+           "oracle": {"tol": 1e-12, "seconds": round(t_or, 2), "cores": cores,
+                      "iters_x": [int(v) for v in info["iters_x"]], "iters_y": [int(v) for v in info["iters_y"]]}}
+    for algo, (X, Y) in acc_cfg["solutions"].items():
+        rx = oracle.true_residual(U, phi, X, lt.L, lt.T, lt.theta, lt.kappa)
+        ry = oracle.true_residual(U, X, Y, lt.L, lt.T, lt.theta, lt.kappa, dagger=True)
+        res[algo] = {"inner": acc_cfg["summary"]["solves"][algo]["inner"],
+                     "err_x": _per_rhs_relerr(X, Xo), "err_y": _per_rhs_relerr(Y, Yo),
+                     "oracle_resid_x": [float(v) for v in rx], "oracle_resid_y": [float(v) for v in ry]}
+    return res
+
+
+def accuracy_config_solves(args, sf, inputs, dev, local_rank):
+    """The 16^4 SF workload (eps 0.2, kappa 0.134, 5 RHS, 1e-10) solved on the
+    GPU with the FP32-inner and the FP16-inner defect correction and with the
+    normal-equation CG route: time, sweeps and inner iterations; the solutions
+    go to the oracle check of the cpu_baseline leg."""
+    import torch
+    w = inputs.workload("sf16_mixed")
+    lt = w.lattices[0]
+    U = lt.make_links()
+    phi = lt.make_sources(w.nrhs)
+    lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(U).to(dev), device=local_rank)
+    phid = torch.from_numpy(phi).to(dev)
+    X, Y = torch.empty_like(phid), torch.empty_like(phid)
+    solves, sols = {}, {}
+    inner = {"mixed_dc": "FP32 BiCGStab", "mixed_dc_half": "FP16-operand BiCGStab", "cg_normal": "FP32 CG on Dhat Dhat^dag"}
+    for algo in ("mixed_dc", "mixed_dc_half", "cg_normal"):
+        sf.solve_block(lat, algo, phid, X, Y, tol=w.tol, maxiter=args.maxiter)   # autotune, graph capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = sf.solve_block(lat, algo, phid, X, Y, tol=w.tol, maxiter=args.maxiter)
+        torch.cuda.synchronize()
+        solves[algo] = {"inner": inner[algo], "ms": round((time.perf_counter() - t0) * 1e3, 2),
+                        "sweeps": [info["iters_outer"], info["iters_outer_y"]],
+                        "inner_iters": [info["iters_inner"], info["iters_inner_y"]],
+                        "library_resid_x": [float(v) for v in info["true_resid"]]}
+        sols[algo] = (X.cpu().numpy(), Y.cpu().numpy())
+    lat.close()
+    summary = {"workload": "sf16_mixed: 16^3x16 SF, eps 0.2, kappa 0.134, theta 0.5, 5 RHS, tol 1e-10 "
+                           "(per-RHS errors against the oracle: cpu_baseline.oracle_check_sf16)",
+               "solves": solves}
+    return {"summary": summary, "solutions": sols, "workload": (w, lt, U, phi)}
+
+
+def hmc_section(args, sf, inputs, lt, U_d, nrhs, tol, fshape, dev, local_rank):
+    """HMC on the bench lattice: the synthetic field is first brought towards
+    equilibrium by MD trajectories accepted unconditionally (untimed), then
+    trajectories with fresh momenta and pseudo-fermions and the Metropolis
+    test are timed; reports dH, the acceptance and the time per trajectory
+    and per accepted trajectory."""
+    import torch
+    hlat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, U_d, device=local_rank)
+    nst, dt = args.hmc_steps, args.hmc_dt
+
+    def draws(k):
+        seed = inputs.SEED_BASE + 600 + k
+        P = torch.from_numpy(inputs.su3_directions(fshape[:2], seed)).to(dev)
+        eta = torch.from_numpy(inputs.sources(lt.L, lt.T, nrhs, seed)).to(dev)
+        u = float(inputs.rng(seed, inputs.FIELD_AUX + 1).random())
+        return P, eta, u
+
+    plaq = [sf.plaquette_action(hlat)]
+    dh_therm = []
+    for k in range(args.hmc_therm):
+        P, eta, _ = draws(k)
+        d = sf.hmc_trajectory(hlat, args.algo, eta, P, -1.0, nst, dt, tol=tol, maxiter=args.maxiter)
+        dh_therm.append(round(d["dH"], 4))
+        plaq.append(sf.plaquette_action(hlat))
+    torch.cuda.synchronize()
+    dhs, acc, ms, iters, launches = [], [], [], 0, 0
+    for k in range(args.hmc_traj):
+        P, eta, u = draws(1000 + k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d = sf.hmc_trajectory(hlat, args.algo, eta, P, u, nst, dt, tol=tol, maxiter=args.maxiter)
+        torch.cuda.synchronize()
+        ms.append(round((time.perf_counter() - t0) * 1e3, 2))
+        dhs.append(round(d["dH"], 5))
+        acc.append(bool(d["accepted"]))
+        iters += d["inner_iters"]
+        launches += d["kernel_launches"]
+    hlat.close()
+    n_acc = sum(acc)
+    V4 = lt.L ** 3 * lt.T * 6
+    return {"workload": f"{lt.L}^3x{lt.T} SF, beta {lt.beta}, {nrhs} pseudo-fermions phi = Dhat eta, Gaussian "
+                        f"momenta, leapfrog {nst} x dt {dt} (trajectory length {nst * dt:g}), {args.algo} to {tol}",
+            "thermalisation": {"trajectories": args.hmc_therm, "accepted": "all (MD only, untimed)",
+                               "dH": dh_therm,
+                               "plaquette_action_per_plaquette": [round(p / (lt.beta * V4), 5) for p in plaq[::max(1, len(plaq) // 8)]]},
+            "trajectories": args.hmc_traj, "dH": dhs, "accepted": acc, "acceptance": round(n_acc / max(1, len(acc)), 3),
+            "ms": ms, "ms_per_trajectory": round(statistics.mean(ms), 2) if ms else None,
+            "ms_per_accepted_trajectory": round(sum(ms) / n_acc, 2) if n_acc else None,
+            "force_evals_per_trajectory": nst + 1, "inner_iters": iters, "kernel_launches": launches}
 
 
 def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle as it stands, full steps of the bench
+    workload (every field's X and Y to 1e-10 and the force) on the host
+    cores, W untimed and K timed."""
     if rank != 0:
         return
     import oracle
@@ -497,23 +623,24 @@ def run_reference(args, rank, world):
     lt = w.lattices[0]
     U = lt.make_links()
     phi = lt.make_sources(w.nrhs)
-    calib = _oracle_calibrate(w, U, phi)
+    cores = _host_cores()
+    oracle.set_num_threads(cores)
     for _ in range(args.warmup):
-        _oracle_step_estimate(w, U, phi, calib, 10)
-    est = []
-    used = 0.0
+        _oracle_full_step(w, U, phi)
+    times = []
+    info = None
     for _ in range(args.steps):
-        e, u = _oracle_step_estimate(w, U, phi, calib, 10)
-        est.append(e)
-        used += u
-    sps = 1.0 / statistics.mean(est)
+        t, _, _, info = _oracle_full_step(w, U, phi)
+        times.append(t)
+    sps = args.steps / sum(times)
     out = {"impl": "reference", "metric": METRIC, "value": round(sps, 6), "unit": UNIT, "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(est) * 1e3, 1),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sum(times) / args.steps * 1e3, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": _workload_desc(args.workload, lt, w.nrhs, w.tol)},
-           "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": round(sps, 6), "unit": UNIT,
-                            "sample": f"per step: 10+10 BiCGStab iterations and one force on one field, scaled by "
-                                      f"the calibrated {calib[0]}+{calib[1]} iterations and {w.nrhs} fields"},
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "value": round(sps, 6), "unit": UNIT,
+                            "sample": f"{args.steps} full steps, measured: {w.nrhs} fields, X and Y by FP64 BiCGStab "
+                                      f"to {w.tol} ({int(np.sum(info['iters_x']))}+{int(np.sum(info['iters_y']))} "
+                                      f"iterations per step) and the force"},
            "e2e": {"value": round(sps, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -645,7 +772,12 @@ def main():
     ap.add_argument("--learned-train-fields", type=int, default=8)
     ap.add_argument("--learned-epochs", type=int, default=15)
     ap.add_argument("--learned-heldout", type=int, default=1)
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-single", action="store_true", help="skip the single-threaded oracle step")
+    ap.add_argument("--no-accuracy-configs", action="store_true")
+    ap.add_argument("--hmc-steps", type=int, default=10)
+    ap.add_argument("--hmc-dt", type=float, default=0.02)
+    ap.add_argument("--hmc-therm", type=int, default=20)
+    ap.add_argument("--hmc-traj", type=int, default=6)
     ap.add_argument("--dslash-only", action="store_true", help="time the hop kernel alone (profiling aid)")
     ap.add_argument("--dslash-lattice", type=int, nargs=2, default=(32, 24), metavar=("L", "T"))
     ap.add_argument("--dslash-precs", default="fp32,fp16")

@@ -308,10 +308,17 @@ sf_status sf_lattice_set_preconditioner(sf_lattice* lat, sf_cnn* cnn);
  * allocate device memory (a runtime or scheduler that owns the whole device,
  * or a fixed memory budget handed out by another framework).  The paper has
  * no counterpart to this call; it exists only for such callers.
- *   links   device pointer, gauge field in the links layout above;
- *   S       host or device pointer to one double (device: written on the
- *           stream, not synchronised; host: the call returns after it);
+ *   links   device (or managed) pointer of `device`, 16-byte aligned, gauge
+ *           field in the links layout above; anything else (a host pointer,
+ *           another device's memory, a misaligned view) gives SF_EINVAL
+ *           before any launch;
+ *   S       pointer to one double: device memory of `device` is written on
+ *           the stream and not synchronised; host or managed memory is
+ *           written before the call returns (the call synchronises the
+ *           stream, so such an S is refused with SF_EINVAL while the stream
+ *           is being captured);
  *   device  CUDA device ordinal of links; stream a cudaStream_t or NULL.
+ * The calling thread's current device is the same after the call as before.
  * Nothing is allocated: the reduction's scratch is a fixed 64.5 KiB array in
  * the library's device image, held by every GPU that loads the library until
  * the process exits.  At most 2097152 gauge sites ((T+1) L^3) per call;

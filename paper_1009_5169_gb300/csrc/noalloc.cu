@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -135,14 +136,32 @@ std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
 
-bool is_device_memory(const void* p) {
+// Where a pointer lives: 0 host (pageable or pinned), 1 device memory of
+// `device`, 2 managed memory, -1 device memory of another device.
+int memory_kind(const void* p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return 2;
+    if (a.type == cudaMemoryTypeDevice) return a.device == device ? 1 : -1;
+    return 0;
 }
+
+// Puts the calling thread's current device back as it found it.
+struct DeviceGuard {
+    int prev = -1;
+    DeviceGuard() {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace
 
@@ -168,9 +187,27 @@ extern "C" sf_status plaquette_action_noalloc(int L, int T, double beta, const d
     if (links == nullptr || S == nullptr) return fail(SF_EINVAL, "links or S is NULL");
     if (!std::isfinite(beta)) return fail(SF_EINVAL, "beta is not finite");
     if (device < 0 || device >= kMaxDevices) return fail(SF_EINVAL, "bad device ordinal");
+    if (reinterpret_cast<uintptr_t>(links) % 16 != 0)
+        return fail(SF_EINVAL, "links must be 16-byte aligned (it is read as pairs of doubles)");
+    if (reinterpret_cast<uintptr_t>(S) % alignof(double) != 0) return fail(SF_EINVAL, "S must be 8-byte aligned");
+    DeviceGuard restore;   // the caller's current device is put back on every return
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return fail(SF_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
-    if (!is_device_memory(links)) return fail(SF_EINVAL, "links must be device memory of the given device");
+    const int links_kind = memory_kind(links, device);
+    if (links_kind != 1 && links_kind != 2)
+        return fail(SF_EINVAL, "links must be device (or managed) memory of device " + std::to_string(device));
+    const int s_kind = memory_kind(S, device);
+    if (s_kind < 0) return fail(SF_EINVAL, "S is device memory of another device");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bool s_on_host_side = (s_kind != 1);   // host or managed: the call waits for the value
+    if (s_on_host_side) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(st, &cs);
+        if (e != cudaSuccess) return fail(SF_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(SF_EINVAL, "S must be device memory while the stream is being captured "
+                                   "(a host or managed S needs a stream synchronisation)");
+    }
     unsigned char* scratch = nullptr;
     {
         std::lock_guard<std::mutex> g(g_mu);
@@ -185,17 +222,16 @@ extern "C" sf_status plaquette_action_noalloc(int L, int T, double beta, const d
         }
         scratch = g_scratch_addr[device];
     }
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     e = cudaMemsetAsync(scratch + kCounterOff, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return fail(SF_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const int blocks = (int)((nsites + kThreads - 1) / kThreads);
     k_plaquette_noalloc<<<blocks, kThreads, 0, st>>>(L, T, beta, reinterpret_cast<const double2*>(links), scratch);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(SF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
-    if (is_device_memory(S)) {
+    if (!s_on_host_side) {
         e = cudaMemcpyAsync(S, scratch + kResultOff, sizeof(double), cudaMemcpyDeviceToDevice, st);
     } else {
-        e = cudaMemcpyAsync(S, scratch + kResultOff, sizeof(double), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(S, scratch + kResultOff, sizeof(double), cudaMemcpyDefault, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     if (e != cudaSuccess) return fail(SF_ECUDA, std::string("result copy: ") + cudaGetErrorString(e));

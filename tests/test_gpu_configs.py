@@ -1,0 +1,141 @@
+"""GPU parity at the workload sizes, against the FP64 oracle.
+
+* 16^4 SF, eps 0.2, kappa 0.134, 5 RHS (the mixed-precision workload; the
+  light-quark, harder solve): the FP32 and FP16 operators against the
+  oracle's Dhat, and the FP32-inner and FP16-inner defect-correction solves
+  and the normal-equation CG route (Sec. 3.2: single-precision inner solve,
+  double-precision solution) judged by the oracle's true residual of every
+  right-hand side, with each RHS's error against the oracle's own solution
+  (solved to 1e-12) reported.
+* 24^4 SF, eps 0.2, kappa 0.134, 5 RHS (the learned-preconditioner
+  workload): the normal-equation route's X and Y judged by the oracle's
+  true residual.
+
+The error of a solution against the oracle's is bounded by the condition
+number times the residual, so it is reported, not gated; the gate on it is
+a sanity bound only (1e-6, four orders above the tolerance).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1009_5169_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL_FACTOR = 1.05   # the oracle's residual may sit a little above the library's (other rounding order)
+
+
+@pytest.fixture(scope="module")
+def sf():
+    from paper_1009_5169_gb300 import binding, build
+    build.build()
+    return binding
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def per_rhs_relerr(a, b):
+    n = a.shape[0]
+    d = np.linalg.norm((a - b).reshape(n, -1), axis=1)
+    return d / np.linalg.norm(b.reshape(n, -1), axis=1)
+
+
+@pytest.fixture(scope="module")
+def sf16():
+    """The 16^4 workload and the oracle's X, Y for all 5 RHS at 1e-12."""
+    w = inputs.workload("sf16_mixed")
+    lt = w.lattices[0]
+    U = lt.make_links()
+    phi = lt.make_sources(w.nrhs)
+    Xo, Yo, info = oracle.solve_pair(U, phi, lt.L, lt.T, lt.theta, lt.kappa, tol=1e-12, maxiter=20000)
+    assert np.all(info["resid_x"] <= 1e-12) and np.all(info["resid_y"] <= 1e-12), info
+    return w, lt, U, phi, Xo, Yo
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 4e-3)])
+def test_sf16_low_precision_operator(sf, sf16, prec, tol):
+    """Dhat and Dhat^dag in FP32 / FP16 (per-site scaled) on the 16^4 field
+    within their storage precision of the oracle's FP64 operator."""
+    w, lt, U, phi, _, _ = sf16
+    lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(U).cuda())
+    xd = torch.from_numpy(phi).cuda()
+    out = torch.empty_like(xd)
+    for op, dag in (("dhat", False), ("dhat_dag", True)):
+        sf.wilson_apply_block(lat, op, prec, xd, out)
+        ref = oracle.apply_dhat(U, phi, lt.L, lt.T, lt.theta, lt.kappa, dagger=dag)
+        assert relerr(out.cpu().numpy(), ref) <= tol, (prec, op)
+    lat.close()
+
+
+@pytest.mark.parametrize("algo", ["mixed_dc", "mixed_dc_half", "cg_normal"])
+def test_sf16_solves_per_rhs_against_oracle(sf, sf16, algo, record_property):
+    """X = Dhat^-1 Phi and Y = Dhat^-dag X at 1e-10 for every RHS of the
+    16^4 kappa 0.134 workload, with the FP32 or FP16 inner solve under the
+    FP64 outer loop; the oracle's residuals judge, the errors against the
+    oracle's solutions are recorded."""
+    w, lt, U, phi, Xo, Yo = sf16
+    lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(U).cuda())
+    phid = torch.from_numpy(phi).cuda()
+    X, Y = torch.empty_like(phid), torch.empty_like(phid)
+    info = sf.solve_block(lat, algo, phid, X, Y, tol=w.tol, maxiter=20000)
+    Xn, Yn = X.cpu().numpy(), Y.cpu().numpy()
+    rx = oracle.true_residual(U, phi, Xn, lt.L, lt.T, lt.theta, lt.kappa)
+    ry = oracle.true_residual(U, Xn, Yn, lt.L, lt.T, lt.theta, lt.kappa, dagger=True)
+    ex, ey = per_rhs_relerr(Xn, Xo), per_rhs_relerr(Yn, Yo)
+    rep = {"algo": algo, "resid_x": rx.tolist(), "resid_y": ry.tolist(), "err_x": ex.tolist(),
+           "err_y": ey.tolist(), "sweeps": [info["iters_outer"], info["iters_outer_y"]],
+           "inner_iters": [info["iters_inner"], info["iters_inner_y"]]}
+    record_property("sf16_" + algo, json.dumps(rep))
+    print("sf16", json.dumps(rep))
+    assert np.all(rx <= w.tol * TOL_FACTOR), rep
+    assert np.all(ry <= w.tol * TOL_FACTOR), rep
+    assert np.all(ex <= 1e-6) and np.all(ey <= 1e-6), rep
+    lat.close()
+
+
+def test_sf16_force_from_gpu_solutions(sf, sf16):
+    """The force of the 16^4 workload from the GPU's X, Y against the
+    oracle's force from the same X, Y (1e-12), and against the oracle's force
+    from its own solutions (reported; bounded by the solutions' error)."""
+    w, lt, U, phi, Xo, Yo = sf16
+    lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(U).cuda())
+    phid = torch.from_numpy(phi).cuda()
+    X, Y = torch.empty_like(phid), torch.empty_like(phid)
+    fshape = ((lt.T + 1) * lt.L ** 3, 4, 8)
+    F = torch.zeros(fshape, dtype=torch.float64, device="cuda")
+    mom = torch.zeros_like(F)
+    sf.md_force_step(lat, "cg_normal", phid, X, Y, F, mom, eps=0.0, tol=w.tol, maxiter=20000)
+    Xn, Yn = X.cpu().numpy(), Y.cpu().numpy()
+    Fg = F.cpu().numpy()
+    Fsame = oracle.force(U, Xn, Yn, lt.L, lt.T, lt.theta, lt.kappa)
+    assert relerr(Fg, Fsame) <= 1e-12
+    Fown = oracle.force(U, Xo, Yo, lt.L, lt.T, lt.theta, lt.kappa)
+    assert relerr(Fg, Fown) <= 1e-6
+    lat.close()
+
+
+def test_sf24_cg_normal_against_oracle_residual(sf):
+    """The 24^4 kappa 0.134 workload solved by the normal-equation route (CG
+    on Dhat Dhat^dag in FP32 under the FP64 outer loop): the oracle's true
+    residuals of X and Y at 1e-10 for every RHS."""
+    w = inputs.workload("sf24_cnn")
+    lt = w.lattices[0]
+    U = lt.make_links()
+    phi = lt.make_sources(w.nrhs)
+    lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(U).cuda())
+    phid = torch.from_numpy(phi).cuda()
+    X, Y = torch.empty_like(phid), torch.empty_like(phid)
+    info = sf.solve_block(lat, "cg_normal", phid, X, Y, tol=w.tol, maxiter=20000)
+    Xn, Yn = X.cpu().numpy(), Y.cpu().numpy()
+    rx = oracle.true_residual(U, phi, Xn, lt.L, lt.T, lt.theta, lt.kappa)
+    ry = oracle.true_residual(U, Xn, Yn, lt.L, lt.T, lt.theta, lt.kappa, dagger=True)
+    assert np.all(rx <= w.tol * TOL_FACTOR), (rx, info)
+    assert np.all(ry <= w.tol * TOL_FACTOR), (ry, info)
+    lat.close()

@@ -62,3 +62,25 @@ def test_noalloc_rejects_oversized_lattice_without_launching(sf):
     rc = _noalloc(sf, 64, 8, 4.52, U, S)   # 9 * 64^3 gauge sites > 2097152
     assert rc == sf.SF_EINVAL
     assert b"2097152" in sf.lib().sf_last_error()
+
+
+def test_noalloc_rejects_bad_links_pointers_without_launching(sf):
+    """A host gauge field, or a device view that is not 16-byte aligned, is
+    refused before any launch (the kernel reads the links as double pairs)."""
+    L, T = 4, 4
+    U = inputs.links(L, T, 0.3, 99)
+    S = ctypes.c_double(0.0)
+    lib = sf.lib()
+    Uh = np.ascontiguousarray(U)   # host memory
+    rc = lib.plaquette_action_noalloc(L, T, 4.52, ctypes.c_void_p(Uh.ctypes.data),
+                                      ctypes.cast(ctypes.byref(S), ctypes.c_void_p), 0, None)
+    assert rc == sf.SF_EINVAL
+    assert b"device" in lib.sf_last_error()
+    flat = torch.from_numpy(U).cuda().view(torch.float64).reshape(-1)
+    shifted = torch.cat([flat, flat[:1]])[1:]   # a view one double past a 256-byte boundary
+    assert shifted.data_ptr() % 16 == 8
+    rc = lib.plaquette_action_noalloc(L, T, 4.52, ctypes.c_void_p(shifted.data_ptr()),
+                                      ctypes.cast(ctypes.byref(S), ctypes.c_void_p), 0, None)
+    assert rc == sf.SF_EINVAL
+    assert b"aligned" in lib.sf_last_error()
+    torch.cuda.synchronize()
