@@ -159,10 +159,13 @@ sf_status sf_lattice_set_links(sf_lattice* lat, const double* links);
  * (1, 2, 3 or 5; FP64: 1 or 2).  A block holds TS * ceil(nrhs / NR) threads,
  * at most 256 (FP64), 320 / 384 / 256 (FP32 and FP16 with NR = 1 / 2 / 3 or
  * 5): checked when a solve or apply uses the
- * tiling, SF_EINVAL beyond.  pipe = 1 selects the pipelined hop (operands of
- * the next hops loaded while the current one is applied; FP32 / FP16 only,
- * NR = 1 or 2, at most 256 threads), pipe = 0 the plain one.  TS = 0
- * restores autotuning (TS, NR and pipe). */
+ * tiling, SF_EINVAL beyond.  pipe selects the hop mode: 0 the plain hop;
+ * 1 the pipelined hop (operands of the next hops loaded while the current
+ * one is applied; FP32 / FP16 only, NR = 1 or 2, at most 256 threads);
+ * 2 links staged per tile (each site's eight links read and their third rows
+ * rebuilt once per block into 18 KiB of shared memory and applied from there
+ * to every right-hand side; FP32 / FP16 only, NR = 1, TS = 32, at most 320
+ * threads).  TS = 0 restores autotuning (TS, NR and pipe). */
 sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR, int pipe);
 
 /* Tiling in use for a precision and block size (runs the autotuner if it has

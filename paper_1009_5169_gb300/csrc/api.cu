@@ -231,7 +231,8 @@ inline bool tiling_ok(int ci, int TS, int NR, int nrhs, int pipe = 0) {
     const int threads = TS * ((nrhs + NR - 1) / NR);
     if (ci == 1 || ci == 2) {
         if (NR != 1 && NR != 2 && NR != 3 && NR != 5) return false;
-        if (pipe) return NR <= 2 && threads <= 256;
+        if (pipe == 2) return NR == 1 && TS == 32 && threads <= 320;   // links staged per tile
+        if (pipe) return pipe == 1 && NR <= 2 && threads <= 256;
         return threads <= (NR == 1 ? 320 : NR == 2 ? 384 : 256);
     }
     if (pipe) return false;
@@ -449,7 +450,8 @@ struct Workspace {
             const int TS = lats[0]->tune_TS[ci], NR = lats[0]->tune_NR[ci], pipe = lats[0]->tune_pipe[ci];
             REQUIRE(tiling_ok(ci, TS, NR, nrhs, pipe),
                     "tiling exceeds the block size of this precision (TS * ceil(nrhs / NR) threads; "
-                    "pipelined hop: FP32 / FP16, NR <= 2, at most 256 threads)");
+                    "pipelined hop: FP32 / FP16, NR <= 2, at most 256 threads; staged links: FP32 / FP16, "
+                    "NR = 1, TS = 32, at most 320 threads)");
             set_tiling(ci, TS, NR, pipe);
             return;
         }
@@ -715,7 +717,7 @@ void Workspace::autotune(int ci) {
         float ms;
     };
     std::vector<Cand> cands;
-    for (int pipe = 0; pipe <= 1; ++pipe)
+    for (int pipe = 0; pipe <= 2; ++pipe)
         for (int NR : nrs_all) {
             if (NR > nrhs) continue;
             for (int TS : tss)
@@ -1462,8 +1464,10 @@ sf_status sf_lattice_set_tuning(sf_lattice* lat, sf_prec prec, int TS, int NR, i
             REQUIRE(TS == 32 || TS == 64 || TS == 128, "TS must be 32, 64 or 128");
             REQUIRE(NR == 1 || NR == 2 || NR == 3 || NR == 5, "NR must be 1, 2, 3 or 5");
             REQUIRE(!(ci == 0 && NR > 2), "FP64 supports NR = 1 or 2");
-            REQUIRE(pipe == 0 || pipe == 1, "pipe must be 0 or 1");
-            REQUIRE(!pipe || (ci != 0 && NR <= 2), "the pipelined hop takes FP32 / FP16 operands and NR = 1 or 2");
+            REQUIRE(pipe >= 0 && pipe <= 2, "pipe (the hop mode) must be 0, 1 or 2");
+            REQUIRE(pipe != 1 || (ci != 0 && NR <= 2), "the pipelined hop takes FP32 / FP16 operands and NR = 1 or 2");
+            REQUIRE(pipe != 2 || (ci != 0 && NR == 1 && TS == 32),
+                    "staged links take FP32 / FP16 operands, NR = 1 and TS = 32");
         }
         lat->tune_TS[ci] = TS;
         lat->tune_NR[ci] = NR;

@@ -1,8 +1,8 @@
 // hop.cuh -- the Wilson hop H_oe / H_eo of the even/odd operator (Sec. 3.1,
 // Eq. 2 with the SF boundaries of Sec. 4) on the SoA field storage, for NR
-// right-hand sides per thread, plain or with the next directions' operands
-// fetched ahead, and the k_hop kernel that applies it to a whole block of
-// lattices.  The fused Dhat tail and the solver kernels build on it
+// right-hand sides per thread, plain, with the next directions' operands
+// fetched ahead, or with each tile's links staged once in shared memory, and
+// the k_hop kernel that applies it to a whole block of lattices.  The fused Dhat tail and the solver kernels build on it
 // (krylov_impl.cuh).
 //   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) lambda_mu psi(x+mu)
 //              + (1 + gamma_mu) U_mu(x-mu)^dag lambda_mu^* psi(x-mu),
@@ -48,12 +48,25 @@ struct KB {
     static constexpr int MAXT = F64 ? 256 : (NR == 1 ? 320 : NR == 2 ? 384 : 256);
     static constexpr int MINB = F64 ? 1 : (NR == 1 ? 2 : 1);
 };
-// hop and tail kernels: the pipelined hop's blocks hold at most 256 threads
-// (up to 255 registers each for the operand buffers)
-template <typename P, int NR, bool PIPE>
+// Hop modes (the HM template argument of the hop and tail kernels):
+//   0  plain: every thread loads and rebuilds the links of its site itself;
+//   1  pipelined: the operands of later directions are loaded ahead (FP32 /
+//      FP16, NR <= 2, blocks of at most 256 threads, up to 255 registers);
+//   2  links staged per tile: FP32 / FP16 operands, one right-hand side per
+//      thread, tiles of 32 sites; the block reads and rebuilds each site's
+//      eight links once into shared memory and all its right-hand-side rows
+//      apply them from there, at 64 registers (six 160-thread blocks per SM).
+template <typename P, int NR, int HM>
 struct KBH {
-    static constexpr int MAXT = PIPE ? 256 : KB<P, NR>::MAXT;
-    static constexpr int MINB = PIPE ? 1 : KB<P, NR>::MINB;
+    static constexpr int MAXT = HM == 2 ? 320 : HM == 1 ? 256 : KB<P, NR>::MAXT;
+    static constexpr int MINB = HM == 2 ? 3 : HM == 1 ? 1 : KB<P, NR>::MINB;
+};
+// the fused tails (more live state than the bare hop): in hop mode 2 held to
+// about 100 registers instead of 64
+template <typename P, int NR, int HM>
+struct KBT {
+    static constexpr int MAXT = KBH<P, NR, HM>::MAXT;
+    static constexpr int MINB = HM == 2 ? 2 : KBH<P, NR, HM>::MINB;
 };
 
 // ------------------------------------------------------------ hop
@@ -256,12 +269,107 @@ __device__ __forceinline__ void hop_site_pipe(const LatDev& g, const SiteX& s, i
     hop_step<7, P, NR, DAG, PF>(g, s, cb, out_par, in, r0, nval, b, v, acc);
 }
 
-// the hop of one site for NR right-hand sides, plain or pipelined
-template <typename P, int NR, bool DAG, bool PIPE>
+// ------------------------------------------------------------ links staged per tile (hop mode 2)
+// Tiles of HOP_SM_TS = 32 sites (blockDim.x); shared memory per block:
+// float2 [8 directions][9 elements][32 sites], the FP32 complex elements of
+// U_mu(x) (direction 2 mu) and U_mu(x - mu) (direction 2 mu + 1), 18 KiB.
+constexpr int HOP_SM_TS = 32;
+constexpr int HOP_SM_BYTES = 8 * 9 * HOP_SM_TS * (int)sizeof(float2);
+
+// All threads of the block: read the links of the tile's sites and rebuild
+// their third rows, once per (site, direction).
+template <typename P>
+__device__ __forceinline__ void stage_tile_links(const LatDev& g, int tile, int out_par, float2* __restrict__ sm) {
+    constexpr int TS = HOP_SM_TS;
+    const int nthr = TS * blockDim.y;
+    for (int li = threadIdx.y * TS + threadIdx.x; li < 8 * TS; li += nthr) {
+        const int dir = li / TS, sl = li % TS;
+        const int cb = tile_cb(g, tile, sl);
+        if (cb < 0) continue;
+        const SiteX s = decode_site(g, cb, out_par);
+        Link<float> U;
+        switch (dir) {
+            case 0: if (s.x0 >= g.T - 1) continue; LinkLoad<P>::template load<0>(g, out_par, cb, U); break;
+            case 1: if (s.x0 <= 1) continue; LinkLoad<P>::template load<0>(g, out_par ^ 1, neighbour_cb<0, -1>(g, s), U); break;
+            case 2: LinkLoad<P>::template load<1>(g, out_par, cb, U); break;
+            case 3: LinkLoad<P>::template load<1>(g, out_par ^ 1, neighbour_cb<1, -1>(g, s), U); break;
+            case 4: LinkLoad<P>::template load<2>(g, out_par, cb, U); break;
+            case 5: LinkLoad<P>::template load<2>(g, out_par ^ 1, neighbour_cb<2, -1>(g, s), U); break;
+            case 6: LinkLoad<P>::template load<3>(g, out_par, cb, U); break;
+            default: LinkLoad<P>::template load<3>(g, out_par ^ 1, neighbour_cb<3, -1>(g, s), U); break;
+        }
+        float2* d = sm + dir * 9 * TS + sl;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) d[k * TS] = make_float2(U.m[k / 3][k % 3].re, U.m[k / 3][k % 3].im);
+    }
+}
+
+template <int MU, bool FWD, typename P, bool DAG>
+__device__ __forceinline__ void hop_dir_staged(const LatDev& g, const SiteX& s, const CField<P>& in, int rhs,
+                                               const float2* __restrict__ sm, cpx<float> (&acc)[4][3]) {
+    if (MU == 0 && (FWD ? s.x0 >= g.T - 1 : s.x0 <= 1)) return;
+    constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma_mu, backward 1 - SF gamma_mu
+    constexpr int S = FWD ? SF : -SF;
+    const int ncb = neighbour_cb<MU, FWD ? +1 : -1>(g, s);
+    cpx<float> p[4][3];
+    load_spinor<P, float>(in, vbase<P>(g, rhs), g.Vpad, ncb, sbase(g, rhs), p);
+    cpx<float> h[2][3], w[2][3];
+    project<MU, S>(p, h);
+    constexpr int TS = HOP_SM_TS;
+    const float2* u = sm + (2 * MU + (FWD ? 0 : 1)) * 9 * TS + threadIdx.x;
+    Link<float> U;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float2 v = u[k * TS];
+        U.m[k / 3][k % 3] = cpx<float>{v.x, v.y};
+    }
+    if (FWD) mul_link(U, h, w);
+    else mul_link_dag(U, h, w);
+    expand_add<MU, S>(acc, w);
+}
+
+template <typename P, bool DAG>
+__device__ __forceinline__ void hop_site_staged(const LatDev& g, const SiteX& s, const CField<P>& in, int rhs,
+                                                const float2* __restrict__ sm, cpx<float> (&acc)[1][4][3]) {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[0][sp][a] = cpx<float>{0.f, 0.f};
+    hop_dir_staged<0, true, P, DAG>(g, s, in, rhs, sm, acc[0]);
+    hop_dir_staged<0, false, P, DAG>(g, s, in, rhs, sm, acc[0]);
+    hop_dir_staged<1, true, P, DAG>(g, s, in, rhs, sm, acc[0]);
+    hop_dir_staged<1, false, P, DAG>(g, s, in, rhs, sm, acc[0]);
+    hop_dir_staged<2, true, P, DAG>(g, s, in, rhs, sm, acc[0]);
+    hop_dir_staged<2, false, P, DAG>(g, s, in, rhs, sm, acc[0]);
+    hop_dir_staged<3, true, P, DAG>(g, s, in, rhs, sm, acc[0]);
+    hop_dir_staged<3, false, P, DAG>(g, s, in, rhs, sm, acc[0]);
+}
+
+// At the top of each tile of a hop-mode-2 kernel: every thread of the block
+// takes part, whether or not its right-hand side is active.
+template <typename P, int HM>
+__device__ __forceinline__ void stage_if_needed(const LatDev& g, int tile, int out_par, float2* sm) {
+    if constexpr (HM == 2) {
+        __syncthreads();   // the previous tile's links are no longer read
+        stage_tile_links<P>(g, tile, out_par, sm);
+        __syncthreads();
+    }
+}
+
+// the hop of one site for NR right-hand sides in hop mode HM (sm: the
+// tile's staged links, mode 2 only)
+template <typename P, int NR, bool DAG, int HM>
 __device__ __forceinline__ void hop_any(const LatDev& g, const SiteX& s, int cb, int out_par, const CField<P>& in,
-                                        int r0, int nval, cpx<typename P::real> (&acc)[NR][4][3]) {
-    if constexpr (PIPE) hop_site_pipe<P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
-    else hop_site<P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+                                        int r0, int nval, cpx<typename P::real> (&acc)[NR][4][3],
+                                        const float2* sm = nullptr) {
+    if constexpr (HM == 2) {
+        static_assert(NR == 1 && !std::is_same<P, P64>::value, "staged links: FP32 / FP16 operands, NR = 1");
+        hop_site_staged<P, DAG>(g, s, in, r0, sm, acc);
+    } else if constexpr (HM == 1) {
+        hop_site_pipe<P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    } else {
+        hop_site<P, NR, DAG>(g, s, cb, out_par, in, r0, nval, acc);
+    }
 }
 
 __device__ __forceinline__ bool rhs_active(const KState* st, int idx) { return st == nullptr || st[idx].active != 0; }
@@ -269,11 +377,12 @@ __device__ __forceinline__ bool rhs_active(const KState* st, int idx) { return s
 
 // ------------------------------------------------------------ kernels
 // out(out_par) = coef * H in
-template <typename PI, typename PO, int NR, bool DAG, bool PIPE>
-__global__ void __launch_bounds__(KBH<PI, NR, PIPE>::MAXT, KBH<PI, NR, PIPE>::MINB) k_hop(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
+template <typename PI, typename PO, int NR, bool DAG, int HM>
+__global__ void __launch_bounds__(KBH<PI, NR, HM>::MAXT, KBH<PI, NR, HM>::MINB) k_hop(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
                                               CField<PI> in, Field<PO> out, double coef, int kpow,
                                               const KState* __restrict__ st) {
     pdl_enter();
+    extern __shared__ float2 hop_sm[];   // hop mode 2: the tile's links
     using R = typename PI::real;
     const int l = find_lattice(lats, nlat, blockIdx.x);
     const LatDev g = lats[l];
@@ -283,14 +392,19 @@ __global__ void __launch_bounds__(KBH<PI, NR, PIPE>::MAXT, KBH<PI, NR, PIPE>::MI
 #pragma unroll
     for (int j = 0; j < NR; ++j)
         if (j < nval && rhs_active(st, l * nrhs + r0 + j)) any = true;
-    if (!any) return;
+    if constexpr (HM == 2) {
+        if (!__syncthreads_or(any)) return;   // block-uniform: the staging needs every thread
+    } else if (!any) {
+        return;
+    }
     const R c = (R)(coef * (kpow == 0 ? 1.0 : kpow == 1 ? g.kappa : g.kappa * g.kappa));
     for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        stage_if_needed<PI, HM>(g, tile, out_par, hop_sm);
         const int cb = tile_cb(g, tile, threadIdx.x);
-        if (cb < 0) continue;
+        if (cb < 0 || !any) continue;
         const SiteX s = decode_site(g, cb, out_par);
         cpx<R> acc[NR][4][3];
-        hop_any<PI, NR, DAG, PIPE>(g, s, cb, out_par, in, r0, nval, acc);
+        hop_any<PI, NR, DAG, HM>(g, s, cb, out_par, in, r0, nval, acc, hop_sm);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (j < nval) {

@@ -325,8 +325,8 @@ __device__ __forceinline__ void norm_acc(const cpx<R> (&a)[4][3], A& n) {
 // *_prev fields and sets the loop condition from the active flags the
 // previous step left (the loop runs one pass with every rhs idle after the
 // last one stops).
-template <typename PH, typename PV, int NR, bool DAG, int RED, bool HASZ, bool PIPE>
-__global__ void __launch_bounds__(KBH<PH, NR, PIPE>::MAXT, KBH<PH, NR, PIPE>::MINB) k_tail(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
+template <typename PH, typename PV, int NR, bool DAG, int RED, bool HASZ, int HM>
+__global__ void __launch_bounds__(KBT<PH, NR, HM>::MAXT, KBT<PH, NR, HM>::MINB) k_tail(const LatDev* __restrict__ lats, int nlat, int nrhs, int out_par,
                                                CField<PH> hin, CField<PV> xv, CField<PV> zv, Field<PV> out,
                                                CField<PV> ra, double a, double coef, int kpow,
                                                SolverCtx ctx) {
@@ -353,13 +353,17 @@ __global__ void __launch_bounds__(KBH<PH, NR, PIPE>::MAXT, KBH<PH, NR, PIPE>::MI
         for (int q = 0; q < NQ; ++q) red[j][q] = acc_zero<A>();
     const RV av = (RV)a;
     const RV cv = (RV)(coef * (kpow == 0 ? 1.0 : kpow == 1 ? g.kappa : g.kappa * g.kappa));
-    if (any) {
+    extern __shared__ float2 hop_sm[];   // hop mode 2: the tile's links
+    bool block_any = any;
+    if constexpr (HM == 2) block_any = __syncthreads_or(any);   // block-uniform: the staging needs every thread
+    if (block_any) {
         for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+            stage_if_needed<PH, HM>(g, tile, out_par, hop_sm);
             const int cb = tile_cb(g, tile, threadIdx.x);
-            if (cb < 0) continue;
+            if (cb < 0 || !any) continue;
             const SiteX s = decode_site(g, cb, out_par);
             cpx<RH> acc[NR][4][3];
-            hop_any<PH, NR, DAG, PIPE>(g, s, cb, out_par, hin, r0, nval, acc);
+            hop_any<PH, NR, DAG, HM>(g, s, cb, out_par, hin, r0, nval, acc, hop_sm);
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
                 if (!act[j]) continue;
@@ -464,8 +468,8 @@ __global__ void __launch_bounds__(KB<PV, NR>::MAXT, KB<PV, NR>::MINB) k_s_update
 // target2, maxiter) no block of this launch writes.  alpha and beta are
 // formed in double (the denominator is a difference) and applied in the
 // vector precision.
-template <typename PV, int NR, bool PIPE>
-__global__ void __launch_bounds__(KBH<PV, NR, PIPE>::MAXT, KBH<PV, NR, PIPE>::MINB) k_cg_tail(
+template <typename PV, int NR, int HM>
+__global__ void __launch_bounds__(KBT<PV, NR, HM>::MAXT, KBT<PV, NR, HM>::MINB) k_cg_tail(
     const LatDev* __restrict__ lats, int nlat, int nrhs, CField<PV> hin, CField<PV> t, Field<PV> x, Field<PV> r,
     Field<PV> p, Field<PV> s, SolverCtx ctx) {
     pdl_enter();
@@ -528,14 +532,20 @@ __global__ void __launch_bounds__(KBH<PV, NR, PIPE>::MAXT, KBH<PV, NR, PIPE>::MI
         be[j] = (j < nval) ? scoef[r0 + j][1] : (RV)0;
         any = any || md[j] != 0;
     }
-    if (!any) return;
+    extern __shared__ float2 hop_sm[];   // hop mode 2: the tile's links
+    if constexpr (HM == 2) {
+        if (!__syncthreads_or(any)) return;   // block-uniform: the staging needs every thread
+    } else if (!any) {
+        return;
+    }
     const RV cv = (RV)(-g.kappa * g.kappa);
     for (int tile = tile_begin(g), tile_end_ = tile_end(g); tile < tile_end_; ++tile) {
+        stage_if_needed<PV, HM>(g, tile, 0, hop_sm);
         const int cb = tile_cb(g, tile, threadIdx.x);
-        if (cb < 0) continue;
+        if (cb < 0 || !any) continue;
         const SiteX site = decode_site(g, cb, 0);
         cpx<RV> acc[NR][4][3];
-        hop_any<PV, NR, false, PIPE>(g, site, cb, 0, hin, r0, nval, acc);
+        hop_any<PV, NR, false, HM>(g, site, cb, 0, hin, r0, nval, acc, hop_sm);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (!md[j]) continue;
@@ -830,20 +840,26 @@ inline dim3 block_of(const LaunchCfg& c) { return dim3(c.TS, (c.nrhs + c.NR - 1)
 
 template <typename PV, typename PH>
 struct OpsImpl {
-    // the pipelined hop: FP32 / FP16 operands, NR <= 2, blocks of <= 256 threads
+    // hop modes (c.pipe): 1 the pipelined hop (FP32 / FP16 operands, NR <= 2,
+    // blocks of <= 256 threads); 2 links staged per tile (FP32 / FP16
+    // operands, NR = 1, TS = 32, blocks of <= 320 threads)
     static bool pipe_ok(const LaunchCfg& c) {
-        return !std::is_same<PH, P64>::value && c.NR <= 2 && c.TS * ((c.nrhs + c.NR - 1) / c.NR) <= 256;
+        if (std::is_same<PH, P64>::value) return false;
+        const int threads = c.TS * ((c.nrhs + c.NR - 1) / c.NR);
+        if (c.pipe == 2) return c.NR == 1 && c.TS == HOP_SM_TS && threads <= 320;
+        return c.pipe == 1 && c.NR <= 2 && threads <= 256;
     }
+    static size_t smem_of(const LaunchCfg& c) { return c.pipe == 2 ? (size_t)HOP_SM_BYTES : 0; }
 
-    template <int NR, bool PIPE>
+    template <int NR, int HM>
     static void hop_nr(const LaunchCfg& c, int out_par, bool dag, FieldPtr in, FieldPtr out, double coef, int kpow,
                        const KState* ks, cudaStream_t st) {
         if (dag)
-            launch_pdl(k_hop<PH, PH, NR, true, PIPE>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
-                       out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
+            launch_pdl_smem(k_hop<PH, PH, NR, true, HM>, dim3(c.nblocks), dim3(block_of(c)), smem_of(c), st, c.lats,
+                            c.nlat, c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
         else
-            launch_pdl(k_hop<PH, PH, NR, false, PIPE>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat,
-                       c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
+            launch_pdl_smem(k_hop<PH, PH, NR, false, HM>, dim3(c.nblocks), dim3(block_of(c)), smem_of(c), st, c.lats,
+                            c.nlat, c.nrhs, out_par, cf<PH>(in), wf<PH>(out), coef, kpow, ks);
     }
 
     static cudaError_t hop(const LaunchCfg& c, int out_par, bool dag, FieldPtr in, FieldPtr out, double coef,
@@ -851,25 +867,35 @@ struct OpsImpl {
         const KState* ks = ctx ? ctx->st : nullptr;
         if (c.pipe && !pipe_ok(c)) return cudaErrorInvalidValue;
         SF_NR_SWITCH(c.NR, {
-            if constexpr (NR_ <= 2 && !std::is_same<PH, P64>::value) {
-                if (c.pipe) hop_nr<NR_, true>(c, out_par, dag, in, out, coef, kpow, ks, st);
-                else hop_nr<NR_, false>(c, out_par, dag, in, out, coef, kpow, ks, st);
-            } else {
-                hop_nr<NR_, false>(c, out_par, dag, in, out, coef, kpow, ks, st);
+            if constexpr (!std::is_same<PH, P64>::value) {
+                if constexpr (NR_ == 1) {
+                    if (c.pipe == 2) {
+                        hop_nr<1, 2>(c, out_par, dag, in, out, coef, kpow, ks, st);
+                        break;
+                    }
+                }
+                if constexpr (NR_ <= 2) {
+                    if (c.pipe == 1) {
+                        hop_nr<NR_, 1>(c, out_par, dag, in, out, coef, kpow, ks, st);
+                        break;
+                    }
+                }
             }
+            hop_nr<NR_, 0>(c, out_par, dag, in, out, coef, kpow, ks, st);
         });
         return cudaGetLastError();
     }
 
-    template <int NR, bool DAG, bool PIPE>
+    template <int NR, bool DAG, int HM>
     static void tail_red(const LaunchCfg& c, int out_par, int red, FieldPtr hin, FieldPtr xv, FieldPtr zv,
                          FieldPtr out, FieldPtr ra, double a, double coef, int kpow, SolverCtx k,
                          double* norm_out, cudaStream_t st) {
         const dim3 b = block_of(c);
         const bool hz = zv.v != nullptr;
 #define SF_TAIL(RED, HZ)                                                                                        \
-    launch_pdl(k_tail<PH, PV, NR, DAG, RED, HZ, PIPE>, dim3(c.nblocks), dim3(b), st, c.lats, c.nlat, c.nrhs,  \
-               out_par, cf<PH>(hin), cf<PV>(xv), cf<PV>(zv), wf<PV>(out), cf<PV>(ra), a, coef, kpow, k)
+    launch_pdl_smem(k_tail<PH, PV, NR, DAG, RED, HZ, HM>, dim3(c.nblocks), dim3(b), smem_of(c), st, c.lats,    \
+                    c.nlat, c.nrhs, out_par, cf<PH>(hin), cf<PV>(xv), cf<PV>(zv), wf<PV>(out), cf<PV>(ra), a, coef, \
+                    kpow, k)
         using A = typename AccOf<typename PV::real>::T;
         using RV = typename PV::real;
         switch (red) {
@@ -901,15 +927,24 @@ struct OpsImpl {
         if (c.pipe && !pipe_ok(c)) return cudaErrorInvalidValue;
         if (red == RED_CG && (!dag || !std::is_same<PV, PH>::value || !ctx || zv.v)) return cudaErrorInvalidValue;
         SF_NR_SWITCH(c.NR, {
-            if constexpr (NR_ <= 2 && !std::is_same<PH, P64>::value) {
-                if (c.pipe) {
-                    if (dag) tail_red<NR_, true, true>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
-                    else tail_red<NR_, false, true>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
-                    break;
+            if constexpr (!std::is_same<PH, P64>::value) {
+                if constexpr (NR_ == 1) {
+                    if (c.pipe == 2) {
+                        if (dag) tail_red<1, true, 2>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+                        else tail_red<1, false, 2>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+                        break;
+                    }
+                }
+                if constexpr (NR_ <= 2) {
+                    if (c.pipe == 1) {
+                        if (dag) tail_red<NR_, true, 1>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+                        else tail_red<NR_, false, 1>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+                        break;
+                    }
                 }
             }
-            if (dag) tail_red<NR_, true, false>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
-            else tail_red<NR_, false, false>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+            if (dag) tail_red<NR_, true, 0>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
+            else tail_red<NR_, false, 0>(c, out_par, red, hin, xv, zv, out, ra, a, coef, kpow, k, norm_out, st);
         });
         return cudaGetLastError();
     }
@@ -952,18 +987,27 @@ struct OpsImpl {
             cudaSuccess)
             return e;
         if ((e = hop(c, 1, false, f.t, f.tmp, 1.0, 0, ctx, st)) != cudaSuccess) return e;
+#define SF_CG_TAIL(HM_)                                                                                          \
+    launch_pdl_smem(k_cg_tail<PV, NR_, HM_>, dim3(c.nblocks), dim3(block_of(c)), smem_of(c), st, c.lats, c.nlat,  \
+                    c.nrhs, cf<PV>(f.tmp), cf<PV>(f.t), wf<PV>(f.x), wf<PV>(f.r), wf<PV>(f.p), wf<PV>(f.s), *ctx)
         SF_NR_SWITCH(c.NR, {
-            if constexpr (NR_ <= 2 && !std::is_same<PH, P64>::value) {
-                if (c.pipe) {
-                    launch_pdl(k_cg_tail<PV, NR_, true>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat,
-                               c.nrhs, cf<PV>(f.tmp), cf<PV>(f.t), wf<PV>(f.x), wf<PV>(f.r), wf<PV>(f.p),
-                               wf<PV>(f.s), *ctx);
-                    break;
+            if constexpr (!std::is_same<PH, P64>::value) {
+                if constexpr (NR_ == 1) {
+                    if (c.pipe == 2) {
+                        SF_CG_TAIL(2);
+                        break;
+                    }
+                }
+                if constexpr (NR_ <= 2) {
+                    if (c.pipe == 1) {
+                        SF_CG_TAIL(1);
+                        break;
+                    }
                 }
             }
-            launch_pdl(k_cg_tail<PV, NR_, false>, dim3(c.nblocks), dim3(block_of(c)), st, c.lats, c.nlat, c.nrhs,
-                       cf<PV>(f.tmp), cf<PV>(f.t), wf<PV>(f.x), wf<PV>(f.r), wf<PV>(f.p), wf<PV>(f.s), *ctx);
+            SF_CG_TAIL(0);
         });
+#undef SF_CG_TAIL
         return cudaGetLastError();
     }
     static int iteration_kernels_cg(const LaunchCfg&) { return 4; }

@@ -54,7 +54,8 @@ struct LaunchCfg {
     int TS;               // sites per tile (multiple of 32)
     int NR;               // right-hand sides per thread (1, 2, 3 or 5)
     int nblocks;          // total blocks (sum of lattice nblk)
-    int pipe;             // 1: pipelined hop (FP32 / FP16, NR <= 2, TS * groups <= 256)
+    int pipe;             // hop mode: 0 plain, 1 pipelined (FP32 / FP16, NR <= 2, TS * groups <= 256),
+                          // 2 links staged per tile (FP32 / FP16, NR = 1, TS 32 or 64, <= 320 threads)
 };
 
 struct SolverCtx {
@@ -119,13 +120,15 @@ struct KrylovOps {
 };
 
 // Launch a kernel of this library with programmatic stream serialization
-// (it starts with pdl_enter(), see sf_device.cuh).
+// (it starts with pdl_enter(), see sf_device.cuh) and smem bytes of dynamic
+// shared memory.
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+inline cudaError_t launch_pdl_smem(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                   Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -133,6 +136,11 @@ inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaSt
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    return launch_pdl_smem(k, grid, block, 0, st, args...);
 }
 
 const KrylovOps& ops_f64();

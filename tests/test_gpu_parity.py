@@ -101,13 +101,15 @@ def test_tilings_agree(sf):
     x = torch.from_numpy(inputs.sources(L, T, 5, 56)).cuda()
     outs = {}
     for prec, nrs in (("fp64", (1, 2)), ("fp32", (1, 2, 3, 5)), ("fp16", (1, 2, 3, 5))):
-        for pipe in ((0,) if prec == "fp64" else (0, 1)):
+        for pipe in ((0,) if prec == "fp64" else (0, 1, 2)):
             for TS in (32, 64, 128):
                 for NR in nrs:
                     RG = -(-5 // NR)
                     lim = {"fp64": 256}.get(prec, 320 if NR == 1 else 384 if NR == 2 else 256)
-                    if pipe:
+                    if pipe == 1:
                         lim = 256 if NR <= 2 else 0
+                    if pipe == 2:   # staged links: NR = 1, TS = 32
+                        lim = 320 if (NR == 1 and TS == 32) else 0
                     if TS * RG > lim:
                         continue
                     lat = sf.Lattice(L, T, theta, kappa, 4.52, torch.from_numpy(U).cuda())
@@ -442,7 +444,8 @@ def test_tiling_validation(sf):
     """Unsupported tilings are refused with SF_EINVAL, nothing launched."""
     U, lat = _lattice(sf, 4, 4, 0.3, 0.125, 0.5)
     for prec, TS, NR, pipe in (("fp32", 96, 1, 0), ("fp16", 64, 4, 0), ("fp64", 48, 1, 0), ("fp64", 32, 3, 0),
-                               ("fp64", 32, 1, 1), ("fp32", 32, 3, 1), ("fp32", 32, 1, 2)):
+                               ("fp64", 32, 1, 1), ("fp32", 32, 3, 1), ("fp32", 32, 1, 3), ("fp32", 64, 1, 2),
+                               ("fp16", 32, 2, 2), ("fp64", 32, 1, 2)):
         with pytest.raises(sf.SFError):
             lat.set_tuning(prec, TS, NR, pipe)
     lat.set_tuning("fp64", 128, 2)   # 128 x 3 rhs groups > 256 threads at NR = 2
@@ -452,4 +455,30 @@ def test_tiling_validation(sf):
     lat.set_tuning("fp32", 128, 2, 1)   # pipelined: 128 x 3 > 256 threads
     with pytest.raises(sf.SFError):
         sf.wilson_apply_block(lat, "dhat", "fp32", x, torch.empty_like(x))
+    lat.set_tuning("fp16", 32, 1, 2)   # staged links: 32 x 16 rhs > 320 threads
+    x16 = torch.from_numpy(inputs.sources(4, 4, 16, 3)).cuda()
+    with pytest.raises(sf.SFError):
+        sf.wilson_apply_block(lat, "dhat", "fp16", x16, torch.empty_like(x16))
+    lat.close()
+
+
+@pytest.mark.parametrize("algo", ["mixed_dc", "mixed_dc_half", "cg_normal"])
+@pytest.mark.parametrize("L,T", [(6, 7), (8, 8)])
+def test_staged_link_tiling_solves(sf, algo, L, T):
+    """The FP32 / FP16 inner solves with every hop and tail kernel in hop mode
+    2 (links staged per tile in shared memory; ragged last tiles at 6^3 x 7)
+    reach the requested residual by the oracle's judgement."""
+    U = inputs.links(L, T, 0.3, 77)
+    phi = inputs.sources(L, T, 5, 78)
+    lat = sf.Lattice(L, T, 0.5, 0.13, 4.52, torch.from_numpy(U).cuda())
+    lat.set_tuning("fp32", 32, 1, 2)
+    lat.set_tuning("fp16", 32, 1, 2)
+    phid = torch.from_numpy(phi).cuda()
+    X, Y = torch.empty_like(phid), torch.empty_like(phid)
+    info = sf.solve_block(lat, algo, phid, X, Y, tol=1e-10, maxiter=5000)
+    assert lat.get_tuning("fp32" if algo != "mixed_dc_half" else "fp16", 5) == (32, 1, 2)
+    Xn, Yn = X.cpu().numpy(), Y.cpu().numpy()
+    rx = oracle.true_residual(U, phi, Xn, L, T, 0.5, 0.13)
+    ry = oracle.true_residual(U, Xn, Yn, L, T, 0.5, 0.13, dagger=True)
+    assert np.all(rx <= 1.05e-10) and np.all(ry <= 1.05e-10), (rx, ry, info)
     lat.close()
