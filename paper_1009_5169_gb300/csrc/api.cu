@@ -147,12 +147,21 @@ struct FieldBuf {
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// SF_NO_GRAPH=1 runs the inner BiCGStab loop without the CUDA graph
+// SF_NO_GRAPH=1 runs the solver loops without CUDA graphs (every kernel
+// launched from the host; for profilers that cannot look into conditional
+// graph nodes).  SF_SWEEP_GRAPHS=1 keeps one graph per defect-correction
+// sweep with the sweeps driven from the host (two synchronisations per
+// sweep) instead of the whole solve in one graph.
+bool env_flag(const char* name) {
+    const char* e = getenv(name);
+    return e != nullptr && e[0] != '\0' && e[0] != '0';
+}
 bool no_graph() {
-    static const bool v = [] {
-        const char* e = getenv("SF_NO_GRAPH");
-        return e != nullptr && e[0] != '\0' && e[0] != '0';
-    }();
+    static const bool v = env_flag("SF_NO_GRAPH");
+    return v;
+}
+bool sweep_graphs() {
+    static const bool v = env_flag("SF_SWEEP_GRAPHS");
     return v;
 }
 
@@ -244,6 +253,7 @@ struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond = 0;
+    long long pro_k = 0, sweep_k = 0;   // graph-resident solve: kernels of the prologue and of one sweep
     ~GraphEntry() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -255,6 +265,7 @@ struct Workspace {
     int nlat = 0, nrhs = 0, device = 0, sm_count = 152;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_top = nullptr, cap_sweep = nullptr;  // capture streams of the graph-resident solve
     long long S = 0;
     std::vector<long long> soff;
 
@@ -278,12 +289,24 @@ struct Workspace {
     DevMem aux;  // per-rhs scalars of the learned preconditioner's training
     int* pin = nullptr;  // pinned: [0] n_active, [1] loop_count
     std::map<int, std::unique_ptr<GraphEntry>> graphs;
+    struct SolveKey {
+        int ci, dag, cg, from_x, maxiter;
+        const void *phi, *x, *odd_dag;
+        bool operator<(const SolveKey& o) const {
+            return std::tie(ci, dag, cg, from_x, maxiter, phi, x, odd_dag) <
+                   std::tie(o.ci, o.dag, o.cg, o.from_x, o.maxiter, o.phi, o.x, o.odd_dag);
+        }
+    };
+    std::map<SolveKey, std::unique_ptr<GraphEntry>> solve_graphs;
     long long launches = 0;
 
     ~Workspace() {
         graphs.clear();
         if (pin) cudaFreeHost(pin);
+        solve_graphs.clear();
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (cap_top) cudaStreamDestroy(cap_top);
+        if (cap_sweep) cudaStreamDestroy(cap_sweep);
     }
 
     void setup(const std::vector<sf_lattice*>& ls, int nr) {
@@ -294,6 +317,8 @@ struct Workspace {
         sm_count = ls[0]->sm_count;
         stream = ls[0]->stream;
         CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&cap_top, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&cap_sweep, cudaStreamNonBlocking));
         soff.resize(nlat);
         S = 0;
         for (int l = 0; l < nlat; ++l) {
@@ -321,7 +346,8 @@ struct Workspace {
         }
         // per-block partial sums of the reductions (3 rows per rhs at most)
         partials.ensure((size_t)3 * nrhs * maxblk * sizeof(double));
-        loop_count.ensure(4 * sizeof(int));  // [0] WHILE iterations, [1] cap, [2] continue flag
+        loop_count.ensure(8 * sizeof(int));  // [0] WHILE iterations, [1] cap, [2] continue flag, [3] solve
+                                             // total, [4] sweeps of the graph-resident solve
         nrm_bb.ensure(n * sizeof(double));
         nrm_rr.ensure(n * sizeof(double));
         n_active.ensure(sizeof(int));
@@ -356,6 +382,7 @@ struct Workspace {
         c.ready = true;
         // graphs bake launch shapes in
         for (int k : {0, 1, 8, 9}) graphs.erase(ci * 2 + k);
+        solve_graphs.clear();
     }
 
     void ensure_inner(int ci) {
@@ -433,6 +460,162 @@ struct Workspace {
         CK(cudaGraphInstantiate(&ge->exec, ge->graph, 0));
         GraphEntry& ref = *ge;
         graphs[key] = std::move(ge);
+        return ref;
+    }
+
+    // ---- one sweep's FP64 residual on stream s: r64 = phi - A x and |r|^2 (A =
+    // Dhat or Dhat^dag; cg: A = Dhat Dhat^dag with w64 = Dhat^dag x first, its
+    // first hop kept in odd_dag).  t64o keeps the first hop of the last
+    // product (the odd-site part of the solution).  copy_kernel: the odd_dag
+    // copy as a kernel (inside the graph-resident solve).
+    void sweep_residual(bool dag, bool cg, const FieldBuf& phi, const FieldBuf& x, FieldBuf* odd_dag, cudaStream_t s,
+                        bool copy_kernel) {
+        if (cg) {
+            const KrylovOps& o64 = ops_f64();
+            CK(o64.hop(cfg[0].lc, 1, true, x.ptr(), t64o.ptr(), 1.0, 1, nullptr, s));
+            if (odd_dag) {
+                if (copy_kernel)
+                    CK(launch_copy_f64(odd_dag->v.as<double>(), t64o.v.as<double>(), 24LL * S, sm_count, s));
+                else
+                    CK(cudaMemcpyAsync(odd_dag->v.p, t64o.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, s));
+                launches += copy_kernel ? 1 : 0;
+            }
+            CK(o64.tail(cfg[0].lc, 0, true, RED_NONE, t64o.ptr(), x.ptr(), FieldPtr{nullptr, nullptr}, w64.ptr(),
+                        FieldPtr{nullptr, nullptr}, 1.0, -1.0, 1, nullptr, nullptr, s));
+            launches += 2;
+            residual64(false, phi, w64, s);
+        } else {
+            residual64(dag, phi, x, s);
+        }
+    }
+
+    // add a WHILE node controlled by h after the work captured so far on s; returns its body graph
+    static cudaGraph_t add_while(cudaStream_t s, cudaGraphConditionalHandle h) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+        alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+        memset(raw, 0, sizeof raw);
+        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+        CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        return cp.conditional.phGraph_out[0];
+    }
+
+    static cudaGraphConditionalHandle new_handle(cudaStream_t s) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+        return h;
+    }
+
+    // ---- the whole defect-correction solve as one graph, launched once per
+    // solve with one host synchronisation at its end: |phi|^2, the first FP64
+    // residual and the check that opens the sweep loop, then a WHILE node over
+    // the sweeps whose body holds the inner start, the WHILE node over the
+    // inner iterations, the update x += |r| e, the next FP64 residual and the
+    // check that decides the next sweep (k_outer_check sets the condition;
+    // every rhs stops after max_sweeps sweeps, so the loop ends).
+    GraphEntry& solve_graph(int ci, bool dag, bool cg, bool from_x, const FieldBuf& phi, FieldBuf& x,
+                            FieldBuf* odd_dag, int maxiter, int max_sweeps, long long& pro_k, long long& sweep_k) {
+        const SolveKey key{ci, dag ? 1 : 0, cg ? 1 : 0, from_x ? 1 : 0, maxiter, phi.v.p, x.v.p,
+                           odd_dag ? odd_dag->v.p : nullptr};
+        auto it = solve_graphs.find(key);
+        if (it != solve_graphs.end()) {
+            pro_k = it->second->pro_k;
+            sweep_k = it->second->sweep_k;
+            return *it->second;
+        }
+        const KrylovOps& o = ops_for(ci);
+        const int n = nlat * nrhs;
+        const long long saved = launches;   // capturing launches nothing
+        auto ge = std::make_unique<GraphEntry>();
+        auto abandon = [](cudaStream_t s) {
+            cudaGraph_t dummy = nullptr;
+            cudaStreamEndCapture(s, &dummy);
+            if (dummy) cudaGraphDestroy(dummy);
+        };
+        CK(cudaStreamBeginCapture(cap_top, cudaStreamCaptureModeThreadLocal));
+        try {
+            const cudaGraphConditionalHandle h_sweep = new_handle(cap_top);
+            launches = 0;
+            SolverCtx k0 = ctx(false);
+            CK(launch_norm2(cfg[0].lc, phi.ptr(), &k0, nrm_bb.as<double>(), cap_top));
+            launches += 2;
+            if (!from_x) {   // x = 0: r = phi; the odd-site parts of x (and of Dhat^dag x) are 0
+                CK(launch_copy_f64(r64.v.as<double>(), phi.v.as<double>(), 24LL * S, sm_count, cap_top));
+                CK(launch_copy_f64(nrm_rr.as<double>(), nrm_bb.as<double>(), n, sm_count, cap_top));
+                CK(launch_copy_f64(t64o.v.as<double>(), nullptr, 24LL * S, sm_count, cap_top));
+                launches += 3;
+                if (cg) {
+                    CK(launch_copy_f64(w64.v.as<double>(), nullptr, 24LL * S, sm_count, cap_top));
+                    launches += 1;
+                    if (odd_dag) {
+                        CK(launch_copy_f64(odd_dag->v.as<double>(), nullptr, 24LL * S, sm_count, cap_top));
+                        launches += 1;
+                    }
+                }
+            } else {
+                sweep_residual(dag, cg, phi, x, odd_dag, cap_top, true);
+            }
+            CK(launch_outer_check(n, ost.as<OState>(), nrm_rr.as<double>(), nrm_bb.as<double>(), max_sweeps,
+                                  n_active.as<int>(), cap_top, h_sweep, 1, loop_count.as<int>() + 4));
+            launches += 1;
+            ge->pro_k = launches;
+            cudaGraph_t body = add_while(cap_top, h_sweep);
+            CK(cudaStreamBeginCaptureToGraph(cap_sweep, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            try {
+                launches = 0;
+                const cudaGraphConditionalHandle h_iter = new_handle(cap_sweep);
+                SolverCtx ki = ctx(true);
+                ki.cond = h_iter;
+                ki.use_cond = 1;
+                Inner& in = inner[ci];
+                CK((cg ? o.init_cg : o.init)(cfg[ci].lc, r64.ptr(), in.x.ptr(), in.r.ptr(), in.r0.ptr(), in.p.ptr(),
+                                             in.ph.ptr(), &ki, maxiter, cap_sweep));
+                cudaGraph_t ibody = add_while(cap_sweep, h_iter);
+                CK(cudaStreamBeginCaptureToGraph(cap_stream, ibody, nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeThreadLocal));
+                try {
+                    enqueue_iteration(ci, dag, ki, cap_stream, cg);
+                } catch (...) {
+                    abandon(cap_stream);
+                    throw;
+                }
+                CK(cudaStreamEndCapture(cap_stream, &ibody));
+                CK(o.dc_update(cfg[ci].lc, x.ptr(), in.x.ptr(), &ki, cap_sweep));
+                launches += 3;   // init (+ its sums), dc_update
+                sweep_residual(dag, cg, phi, x, odd_dag, cap_sweep, true);
+                CK(launch_outer_check(n, ost.as<OState>(), nrm_rr.as<double>(), nullptr, max_sweeps,
+                                      n_active.as<int>(), cap_sweep, h_sweep, 1, loop_count.as<int>() + 4));
+                launches += 1;
+                ge->sweep_k = launches;
+            } catch (...) {
+                abandon(cap_sweep);
+                throw;
+            }
+            CK(cudaStreamEndCapture(cap_sweep, &body));
+        } catch (...) {
+            launches = saved;
+            abandon(cap_top);
+            throw;
+        }
+        launches = saved;
+        CK(cudaStreamEndCapture(cap_top, &ge->graph));
+        CK(cudaGraphInstantiate(&ge->exec, ge->graph, 0));
+        pro_k = ge->pro_k;
+        sweep_k = ge->sweep_k;
+        GraphEntry& ref = *ge;
+        solve_graphs[key] = std::move(ge);
         return ref;
     }
 
@@ -590,16 +773,29 @@ struct Workspace {
         }
         CK(cudaMemcpyAsync(ost.p, oh.data(), n * sizeof(OState), cudaMemcpyHostToDevice, s));
         if (!from_x) CK(cudaMemsetAsync(x.v.p, 0, field_bytes(Prec::F64, S), s));
+        pin[2] = maxiter + 8;  // WHILE cap
+        pin[5] = 0;            // iterations of this solve
+        pin[6] = 0;            // sweeps of the graph-resident solve
+        CK(cudaMemcpyAsync(loop_count.as<int>() + 1, pin + 2, sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(loop_count.as<int>() + 3, pin + 5, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (!no_graph() && !sweep_graphs()) {
+            // the whole solve on the device: one graph launch, one synchronisation
+            long long pro_k = 0, sweep_k = 0;
+            GraphEntry& sg = solve_graph(ci, dag, cg, from_x, phi, x, odd_dag, maxiter, max_sweeps, pro_k, sweep_k);
+            CK(cudaGraphLaunch(sg.exec, s));
+            if (odd) CK(cudaMemcpyAsync(odd->v.p, t64o.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, s));
+            std::vector<OState> out(n);
+            CK(cudaMemcpyAsync(out.data(), ost.p, n * sizeof(OState), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(pin + 5, loop_count.as<int>() + 3, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            launches += pro_k + sweep_k * pin[6] +
+                        (long long)(cg ? o.iteration_kernels_cg : o.iteration_kernels)(cfg[ci].lc) * pin[5];
+            return result_of(out);
+        }
         SolverCtx k0 = ctx(false);
         CK(launch_norm2(cfg[0].lc, phi.ptr(), &k0, nrm_bb.as<double>(), s));
         launches += 2;
-        GraphEntry& ge = graph(ci, dag, cg);
-        pin[2] = maxiter + 8;  // WHILE cap
-        pin[5] = 0;            // iterations of this solve
-        CK(cudaMemcpyAsync(loop_count.as<int>() + 1, pin + 2, sizeof(int), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(loop_count.as<int>() + 3, pin + 5, sizeof(int), cudaMemcpyHostToDevice, s));
         SolverCtx k = ctx(true);
-        Result res;
         bool have_odd = false;  // t64o holds kappa H_oe x of the current x
         for (int sweep = 0;; ++sweep) {
             if (sweep == 0 && !from_x) {
@@ -607,20 +803,10 @@ struct Workspace {
                 CK(cudaMemcpyAsync(r64.v.p, phi.v.p, field_bytes(Prec::F64, S), cudaMemcpyDeviceToDevice, s));
                 CK(cudaMemcpyAsync(nrm_rr.p, nrm_bb.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
                 have_odd = false;
-            } else if (cg) {
-                // w = Dhat^dag x with its first hop kappa gamma5 H_oe gamma5 x (the odd part of x
-                // as the adjoint solution), then r = phi - Dhat w (first hop: the odd part of w)
-                const KrylovOps& o64 = ops_f64();
-                CK(o64.hop(cfg[0].lc, 1, true, x.ptr(), t64o.ptr(), 1.0, 1, nullptr, s));
-                if (odd_dag) CK(cudaMemcpyAsync(odd_dag->v.p, t64o.v.p, field_bytes(Prec::F64, S),
-                                                cudaMemcpyDeviceToDevice, s));
-                CK(o64.tail(cfg[0].lc, 0, true, RED_NONE, t64o.ptr(), x.ptr(), FieldPtr{nullptr, nullptr}, w64.ptr(),
-                            FieldPtr{nullptr, nullptr}, 1.0, -1.0, 1, nullptr, nullptr, s));
-                launches += 2;
-                residual64(false, phi, w64, s);
-                have_odd = true;
             } else {
-                residual64(dag, phi, x, s);
+                // cg: w = Dhat^dag x with its first hop kappa gamma5 H_oe gamma5 x (the odd part of
+                // x as the adjoint solution), then r = phi - Dhat w (first hop: the odd part of w)
+                sweep_residual(dag, cg, phi, x, odd_dag, s, false);
                 have_odd = true;
             }
             CK(launch_outer_check((int)n, ost.as<OState>(), nrm_rr.as<double>(),
@@ -643,7 +829,7 @@ struct Workspace {
                     if (!pin[3]) break;
                 }
             } else {
-                CK(cudaGraphLaunch(ge.exec, s));
+                CK(cudaGraphLaunch(graph(ci, dag, cg).exec, s));
             }
             CK(o.dc_update(cfg[ci].lc, x.ptr(), inner[ci].x.ptr(), &k, s));
             launches += 3;  // init (+ its sums), dc_update
@@ -661,6 +847,12 @@ struct Workspace {
         CK(cudaMemcpyAsync(pin + 5, loop_count.as<int>() + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         launches += (long long)(cg ? o.iteration_kernels_cg : o.iteration_kernels)(cfg[ci].lc) * pin[5];
+        return result_of(out);
+    }
+
+    static Result result_of(const std::vector<OState>& out) {
+        Result res;
+        const size_t n = out.size();
         res.sweeps.resize(n);
         res.inner.resize(n);
         res.resid.resize(n);

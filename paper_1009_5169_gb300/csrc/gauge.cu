@@ -1,6 +1,7 @@
 // gauge.cu -- gauge-field kernels: link preparation into the hop layouts,
 // the SU(3) check of an input field, the SF plaquette action (Sec. 4) and the
 // MD force of Eq. (3) summed over the pseudo-fermion fields (the force steps of Alg. 2).
+#include <algorithm>
 #include <type_traits>
 
 #include "krylov_impl.cuh"
@@ -323,7 +324,8 @@ cudaError_t launch_force(const LaunchCfg& c, FieldPtr xe, FieldPtr xo, FieldPtr 
 
 // ------------------------------------------------------------ misc
 __global__ void k_outer_check(int n, OState* __restrict__ ost, const double* __restrict__ rr,
-                              const double* __restrict__ bb, int max_sweeps, int* n_active) {
+                              const double* __restrict__ bb, int max_sweeps, int* n_active,
+                              cudaGraphConditionalHandle cond, int use_cond, int* sweeps_run) {
     pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int cnt = 0;
@@ -344,11 +346,33 @@ __global__ void k_outer_check(int n, OState* __restrict__ ost, const double* __r
         }
     }
     *n_active = cnt;
+    if (use_cond) {
+        // the graph-resident solve: another sweep while any rhs is active
+        if (cnt > 0 && sweeps_run) *sweeps_run += 1;
+        cudaGraphSetConditional(cond, cnt > 0 ? 1u : 0u);
+    }
 }
 
 cudaError_t launch_outer_check(int n, OState* ost, const double* rr, const double* bb, int max_sweeps,
-                               int* n_active, cudaStream_t st) {
-    launch_pdl(k_outer_check, dim3(1), dim3(32), st, n, ost, rr, bb, max_sweeps, n_active);
+                               int* n_active, cudaStream_t st, cudaGraphConditionalHandle cond, int use_cond,
+                               int* sweeps_run) {
+    launch_pdl(k_outer_check, dim3(1), dim3(32), st, n, ost, rr, bb, max_sweeps, n_active, cond, use_cond,
+               sweeps_run);
+    return cudaGetLastError();
+}
+
+// dst = src (or 0 when src is NULL), n doubles, as a kernel: the copies
+// inside the graph-resident solve stay kernel nodes
+__global__ void k_copy_f64(double* __restrict__ dst, const double* __restrict__ src, long long n) {
+    pdl_enter();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src ? src[i] : 0.0;
+}
+
+cudaError_t launch_copy_f64(double* dst, const double* src, long long n, int sm_count, cudaStream_t st) {
+    const long long want = (n + 255) / 256;
+    const int blocks = (int)std::max(1LL, std::min<long long>(want, 4LL * sm_count));
+    launch_pdl(k_copy_f64, dim3(blocks), dim3(256), st, dst, src, n);
     return cudaGetLastError();
 }
 

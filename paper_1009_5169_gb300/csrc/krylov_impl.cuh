@@ -281,7 +281,11 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(const LatDev* __restrict
     const int tid = threadIdx.x;
     lattice_sums<NQ, A>(ctx.partials, nrhs, nblocks, lats[l].blk0, lats[l].nblk, tid, (int)blockDim.x, sres);
     __syncthreads();
-    if ((MODE == FIN_INIT || MODE == FIN_INIT_CG) && l == 0 && tid == 0) *ctx.loop_count = 0;
+    if ((MODE == FIN_INIT || MODE == FIN_INIT_CG) && l == 0 && tid == 0) {
+        *ctx.loop_count = 0;
+        // inside the graph-resident solve: start the iteration loop of this sweep
+        if (ctx.use_cond) cudaGraphSetConditional(ctx.cond, 1u);
+    }
     if (tid < nrhs) fin_apply<MODE, RV>(ctx, l * nrhs + tid, tid, sres, out, maxiter);
 }
 

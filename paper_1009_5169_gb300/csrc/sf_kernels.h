@@ -149,8 +149,14 @@ const KrylovOps& ops_f32h16();
 
 // FP64 defect-correction control: sets OState.active / inv_norm from the
 // residual norms; writes the number of active rhs to *n_active.
+// In the graph-resident solve (use_cond) it also sets the sweep loop's
+// condition (any rhs active) and counts the sweeps that start.
 cudaError_t launch_outer_check(int n, OState* ost, const double* rr, const double* bb_or_null, int max_sweeps,
-                               int* n_active, cudaStream_t);
+                               int* n_active, cudaStream_t, cudaGraphConditionalHandle cond = 0, int use_cond = 0,
+                               int* sweeps_run = nullptr);
+// dst = src (src NULL: dst = 0), n doubles, as a kernel (kept a kernel node
+// inside the graph-resident solve)
+cudaError_t launch_copy_f64(double* dst, const double* src, long long n, int sm_count, cudaStream_t st);
 // |f|^2 per (lattice, rhs) of an FP64 field
 cudaError_t launch_norm2(const LaunchCfg&, FieldPtr f64, const SolverCtx*, double* out, cudaStream_t);
 

@@ -1,0 +1,59 @@
+"""The three ways the solvers can be driven -- the whole defect-correction
+solve in one CUDA graph (the default), one graph per sweep with the sweeps
+driven from the host (SF_SWEEP_GRAPHS=1), and every kernel launched from the
+host (SF_NO_GRAPH=1) -- run the same kernels in the same order, so X and Y
+agree bitwise.  Each mode runs in a fresh process (the library reads the
+switches once)."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1009_5169_gb300 import binding as sf, inputs
+L, T = 6, 7
+U = inputs.links(L, T, 0.3, 321)
+phi = inputs.sources(L, T, 5, 322)
+lat = sf.Lattice(L, T, 0.5, 0.13, 4.52, torch.from_numpy(U).cuda())
+out = {{}}
+for algo in ("mixed_dc", "mixed_dc_half", "cg_normal", "bicgstab"):
+    p = torch.from_numpy(phi).cuda()
+    X, Y = torch.empty_like(p), torch.empty_like(p)
+    info = sf.solve_block(lat, algo, p, X, Y, tol=1e-10, maxiter=3000)
+    out[algo + "_X"] = X.cpu().numpy()
+    out[algo + "_Y"] = Y.cpu().numpy()
+    out[algo + "_it"] = np.array([info["iters_inner"], info["iters_inner_y"], info["iters_outer"], info["iters_outer_y"]])
+np.savez({path!r}, **out)
+"""
+
+
+def _run(tmp_path, name, env_extra):
+    path = str(tmp_path / f"{name}.npz")
+    env = dict(os.environ)
+    env.pop("SF_NO_GRAPH", None)
+    env.pop("SF_SWEEP_GRAPHS", None)
+    env.update(env_extra)
+    r = subprocess.run([sys.executable, "-c", SCRIPT.format(root=ROOT, path=path)], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return np.load(path)
+
+
+def test_graph_modes_agree_bitwise(tmp_path):
+    from paper_1009_5169_gb300 import build
+    build.build()
+    whole = _run(tmp_path, "whole", {})
+    sweep = _run(tmp_path, "sweep", {"SF_SWEEP_GRAPHS": "1"})
+    plain = _run(tmp_path, "plain", {"SF_NO_GRAPH": "1"})
+    for k in whole.files:
+        assert np.array_equal(whole[k], sweep[k]), k
+        assert np.array_equal(whole[k], plain[k]), k
