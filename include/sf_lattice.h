@@ -124,7 +124,19 @@ typedef enum {
      * the recomputed FP64 residual while a rhs is above tol.  iters_inner
      * reports the block iterations (each applies Dhat to every rhs twice),
      * iters_outer the restarts + 1.  One lattice only (not batches). */
-    SF_SOLVE_BL_BICGSTAB = 7
+    SF_SOLVE_BL_BICGSTAB = 7,
+    /* the learned preconditioner in mixed precision: FP64 defect correction
+     * (r = phi - Dhat x recomputed in FP64, x += |r| e) around flexible GCR in
+     * FP32 (16 directions, FP32 hop, float-float dot products) on
+     * Dhat e = r / |r| to the relative target max(1e-5, 0.1 tol |phi| / |r|),
+     * preconditioned by the attached network on the FP32 residual; the FP64
+     * true residual judges, FP32-inner BiCGStab continues if the sweeps run
+     * out above tol.  iters_outer: sweeps, iters_inner: FGCR iterations.
+     * One lattice only (not batches), nrhs <= 8. */
+    SF_SOLVE_FGCR_CNN_MIXED = 8,
+    /* the same with the identity as preconditioner (the comparison without
+     * the network) */
+    SF_SOLVE_FGCR_MIXED = 9
 } sf_algo;
 
 typedef struct {
@@ -302,6 +314,14 @@ sf_status sf_cnn_train_step(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double
  * (flat layout as the parameters), without updating them. */
 sf_status sf_cnn_gradients(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double* r, const double* e, float* grad,
                            double* loss);
+
+/* Which kernels run the network's convolutions: impl = 0 (the default) the
+ * tcgen05 tensor-core kernel wherever the layer shape fits its shared memory
+ * (hidden width 16; the rest on mma.sync), impl = 1 mma.sync everywhere (a
+ * reference for comparisons).  The weight gradients always use mma.sync.
+ * SF_EINVAL for another impl.  A convolution whose internal wait timed out
+ * makes the next call that synchronises return SF_ECUDA. */
+sf_status sf_cnn_set_conv_impl(sf_cnn* cnn, int impl);
 
 /* Attach a network as the preconditioner of SF_SOLVE_FGCR_CNN on this
  * lattice (NULL detaches; the lattice does not own it). */

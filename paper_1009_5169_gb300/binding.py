@@ -28,7 +28,7 @@ STATUS = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOMEM", 3: "SF_ECUDA", 4: "SF_ENOC
 OPS = {"dhat": 0, "dhat_dag": 1, "dhatdag_dhat": 2, "d_full": 3, "hop_eo": 4, "hop_oe": 5}
 PRECS = {"fp64": 0, "fp32": 1, "fp16": 2}
 ALGOS = {"bicgstab": 0, "mixed_dc": 1, "mixed_dc_half": 2, "fgcr_cnn": 3, "fgcr": 4, "cg_normal": 5,
-         "gl_bicgstab": 6, "bl_bicgstab": 7}
+         "gl_bicgstab": 6, "bl_bicgstab": 7, "fgcr_cnn_mixed": 8, "fgcr_mixed": 9}
 
 
 class SFError(RuntimeError):
@@ -109,8 +109,9 @@ def lib() -> ctypes.CDLL:
         L.sf_cnn_train_step.argtypes = [vp, vp, i, vp, vp, ctypes.c_float, ctypes.POINTER(d)]
         L.sf_cnn_gradients.argtypes = [vp, vp, i, vp, vp, vp, ctypes.POINTER(d)]
         L.sf_lattice_set_preconditioner.argtypes = [vp, vp]
+        L.sf_cnn_set_conv_impl.argtypes = [vp, i]
         for fn in ("sf_cnn_create", "sf_cnn_get_params", "sf_cnn_forward", "sf_cnn_train_step", "sf_cnn_gradients",
-                   "sf_lattice_set_preconditioner"):
+                   "sf_lattice_set_preconditioner", "sf_cnn_set_conv_impl"):
             getattr(L, fn).restype = ctypes.c_int
         L.sf_last_error.restype = ctypes.c_char_p
         L.sf_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), i]
@@ -442,6 +443,11 @@ class Cnn:
         loss = ctypes.c_double()
         _check(lib().sf_cnn_gradients(self._h, lat.handle, nrhs, _ptr(r), _ptr(e), _ptr(g), ctypes.byref(loss)))
         return g, loss.value
+
+    def set_conv_impl(self, impl: str) -> None:
+        """"tcgen05" (the default: the tensor-core convolution where the layer
+        shape fits) or "mma_sync" (the mma.sync kernel everywhere)."""
+        _check(lib().sf_cnn_set_conv_impl(self._h, {"tcgen05": 0, "mma_sync": 1}[impl]))
 
     def close(self) -> None:
         if self._h:

@@ -691,6 +691,16 @@ struct Workspace {
 
     Result fgcr(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
 
+    // ---- FP64 defect correction around an FP32 flexible GCR (16 directions)
+    // preconditioned by the learned network (or the identity)
+    struct Fgcr32 {
+        static constexpr int M = 16;
+        FieldBuf z[M], w[M], r, e, g5a, g5b;
+        DevMem ptrs, rptr, coef, dots, norms, invn, scale, mdot;
+    };
+    std::unique_ptr<Fgcr32> f32;
+    Result fgcr_mixed(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
+
     // ---- Gl-BiCGStab (FP64, Frobenius inner products over the block) with
     // FP32-inner BiCGStab solves as its preconditioner
     struct Gl {
@@ -1053,6 +1063,7 @@ Workspace::Result Workspace::fgcr(bool use_cnn, bool dag, const FieldBuf& phi, F
                 }
                 launches += 8;
                 CK(cudaStreamSynchronize(s));  // the host arrays above are reused next iteration
+                CK(cnn_check(cnn));
             } else {
                 CK(cudaMemcpyAsync(zk.v.p, fg->r.v.p, fbytes, cudaMemcpyDeviceToDevice, s));
             }
@@ -1106,6 +1117,228 @@ Workspace::Result Workspace::fgcr(bool use_cnn, bool dag, const FieldBuf& phi, F
     for (int i = 0; i < n; ++i) {
         res.resid[i] = bb[i] > 0 ? sqrt(rt[i] / bb[i]) : 0.0;
         if (!(rt[i] <= tol * tol * bb[i])) ok = false;
+    }
+    if (ok) return res;
+    Result fb = solve(1, dag, phi, x, tol, maxiter, /*from_x=*/true);
+    for (int i = 0; i < n; ++i) {
+        res.sweeps[i] += fb.sweeps[i];
+        res.inner[i] += fb.inner[i];
+        res.resid[i] = fb.resid[i];
+    }
+    res.converged = fb.converged;
+    return res;
+}
+
+// The learned preconditioner in its mixed-precision form: an FP64 defect
+// correction (r = phi - Dhat x in FP64, x += |r| e) whose inner solve
+// Dhat e = r / |r| is flexible GCR in FP32 -- the FP32 hop and Dhat tail,
+// FP32 vectors with float-float dot products, one pass of classical
+// Gram-Schmidt on the Dhat-images -- with z = M(r) from the network on the
+// FP32 residual (M^dag(r) = gamma5 M(gamma5 r) for the adjoint system), to
+// the relative target max(1e-5, 0.1 tol |phi| / |r|) of the FP32 inner solves.
+// The FP64 true residual judges; FP32-inner BiCGStab continues if the sweeps
+// run out above tol.
+Workspace::Result Workspace::fgcr_mixed(bool use_cnn, bool dag, const FieldBuf& phi, FieldBuf& x, double tol,
+                                        int maxiter) {
+    REQUIRE(nlat == 1, "FGCR runs on a single lattice");
+    REQUIRE(nrhs <= 8, "FGCR, Gl-BiCGStab and Bl-BiCGStab take up to 8 right-hand sides (one 32-site row per rhs)");
+    ensure_cfg(0);
+    ensure_cfg(1);
+    ensure_cfg(3);
+    ensure_inner(1);
+    sf_cnn* cnn = lats[0]->cnn;
+    if (use_cnn) REQUIRE(cnn != nullptr, "no learned preconditioner attached (sf_lattice_set_preconditioner)");
+    cudaStream_t s = stream;
+    const int n = nrhs, m = Fgcr32::M;
+    if (!f32) {
+        f32.reset(new Fgcr32());
+        for (int k = 0; k < m; ++k) {
+            f32->z[k].alloc(Prec::F32, S);
+            f32->w[k].alloc(Prec::F32, S);
+        }
+        f32->r.alloc(Prec::F32, S);
+        f32->e.alloc(Prec::F32, S);
+        f32->g5a.alloc(Prec::F32, S);
+        f32->g5b.alloc(Prec::F32, S);
+        std::vector<void*> p(2 * m);
+        for (int k = 0; k < m; ++k) {
+            p[k] = f32->z[k].v.p;
+            p[m + k] = f32->w[k].v.p;
+        }
+        f32->ptrs.ensure(p.size() * sizeof(void*));
+        CK(cudaMemcpy(f32->ptrs.p, p.data(), p.size() * sizeof(void*), cudaMemcpyHostToDevice));
+        const void* rp = f32->r.v.p;
+        f32->rptr.ensure(sizeof(void*));
+        CK(cudaMemcpy(f32->rptr.p, &rp, sizeof(void*), cudaMemcpyHostToDevice));
+        f32->mdot.ensure((size_t)2 * (m + 2) * n * cfg[3].lc.nblocks * sizeof(double));
+        f32->coef.ensure((size_t)2 * m * n * sizeof(double2));
+        f32->dots.ensure((size_t)2 * m * n * sizeof(double2));
+        f32->norms.ensure((size_t)n * sizeof(double));
+        f32->invn.ensure((size_t)n * sizeof(double));
+        f32->scale.ensure((size_t)n * sizeof(double));
+    }
+    Fgcr32& F = *f32;
+    const float4* const* zp = F.ptrs.as<const float4*>();
+    const float4* const* wp = zp + m;
+    const LaunchCfg& bl = cfg[3].lc;
+    const LaunchCfg& lc32 = cfg[1].lc;
+    const KrylovOps& o32 = ops_f32();
+    const FieldPtr none{nullptr, nullptr};
+    const size_t fbytes64 = field_bytes(Prec::F64, S), fbytes32 = field_bytes(Prec::F32, S);
+    std::vector<double2> hd((size_t)2 * m * n), hc((size_t)2 * m * n);
+    auto read_dots = [&](int count) {
+        CK(cudaMemcpyAsync(hd.data(), F.dots.p, (size_t)count * n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    };
+    auto axpy = [&](const float4* const* xs, int nvec, FieldBuf& y) {
+        CK(cudaMemcpyAsync(F.coef.p, hc.data(), (size_t)nvec * n * sizeof(double2), cudaMemcpyHostToDevice, s));
+        CK(launch_multi_axpy32(bl, nvec, xs, F.coef.as<double2>(), y.ptr(), s));
+        launches += 1;
+    };
+    auto apply32 = [&](const FieldBuf& in, FieldBuf& out) {   // out = Dhat in (Dhat^dag for dag), FP32
+        CK(o32.hop(lc32, 1, dag, in.ptr(), inner[1].tmp.ptr(), 1.0, 0, nullptr, s));
+        CK(o32.tail(lc32, 0, dag, RED_NONE, inner[1].tmp.ptr(), in.ptr(), none, out.ptr(), none, 1.0, -1.0, 2, nullptr,
+                    nullptr, s));
+        launches += 2;
+    };
+    auto set_scale = [&](const std::vector<double>& v) {
+        CK(cudaMemcpyAsync(F.scale.p, v.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    };
+    // outer FP64: x = 0, r = phi
+    CK(cudaMemsetAsync(x.v.p, 0, fbytes64, s));
+    CK(cudaMemcpyAsync(r64.v.p, phi.v.p, fbytes64, cudaMemcpyDeviceToDevice, s));
+    {
+        SolverCtx k0 = ctx(false);
+        CK(launch_norm2(cfg[0].lc, phi.ptr(), &k0, nrm_bb.as<double>(), s));
+        launches += 2;
+    }
+    std::vector<double> bb(n), rr(n);
+    CK(cudaMemcpyAsync(bb.data(), nrm_bb.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    rr = bb;
+    const CnnLatticeView view{cfg[0].host[0], lats[0]->canon.as<double>(), s, n};
+    const double nreal = 24.0 * lats[0]->Vh;
+    const int max_sweeps = 12;
+    std::vector<int> iters(n, 0), sweeps(n, 0);
+    std::vector<double> nw((size_t)m * n), hn(n), hi(n), rin(n), target(n), sc(n);
+    std::vector<char> done(n);
+    int total = 0;
+    for (int sweep = 0; sweep < max_sweeps && total < maxiter; ++sweep) {
+        bool any = false;
+        for (int i = 0; i < n; ++i) {
+            const bool act = bb[i] > 0 && rr[i] > tol * tol * bb[i] && std::isfinite(rr[i]);
+            sc[i] = act ? 1.0 / sqrt(rr[i]) : 0.0;
+            done[i] = !act;
+            rin[i] = act ? 1.0 : 0.0;
+            // the inner relative target: the FP32 floor, or what tol still needs
+            target[i] = act ? std::max(1e-5, 0.1 * tol * sqrt(bb[i] / rr[i])) : 0.0;
+            if (act) {
+                any = true;
+                sweeps[i] += 1;
+            }
+        }
+        if (!any) break;
+        // inner: Dhat e = r / |r| in FP32
+        set_scale(sc);
+        CK(launch_to32(bl, r64.ptr(), F.scale.as<double>(), F.r.ptr(), s));
+        CK(cudaMemsetAsync(F.e.v.p, 0, fbytes32, s));
+        launches += 1;
+        auto inner_done = [&] {
+            for (char d : done)
+                if (!d) return false;
+            return true;
+        };
+        while (!inner_done() && total < maxiter) {
+            for (int k = 0; k < m && !inner_done() && total < maxiter; ++k) {
+                FieldBuf& zk = F.z[k];
+                FieldBuf& wk = F.w[k];
+                if (use_cnn) {
+                    for (int i = 0; i < n; ++i) {
+                        hn[i] = sqrt(rin[i] / nreal);   // RMS scale of the inner residual
+                        hi[i] = hn[i] > 0 ? 1.0 / hn[i] : 0.0;
+                    }
+                    CK(cudaMemcpyAsync(F.norms.p, hn.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+                    CK(cudaMemcpyAsync(F.invn.p, hi.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+                    const long long planes = (long long)S / lats[0]->Vpad * 6;
+                    if (dag) {
+                        CK(launch_gamma5_32(planes, lats[0]->Vpad, F.r.ptr(), F.g5a.ptr(), sm_count, s));
+                        CK(cnn_apply_field32(cnn, view, F.g5a.ptr(), F.norms.as<double>(), F.invn.as<double>(),
+                                             F.g5b.ptr()));
+                        CK(launch_gamma5_32(planes, lats[0]->Vpad, F.g5b.ptr(), zk.ptr(), sm_count, s));
+                    } else {
+                        CK(cnn_apply_field32(cnn, view, F.r.ptr(), F.norms.as<double>(), F.invn.as<double>(),
+                                             zk.ptr()));
+                    }
+                    launches += 8;
+                } else {
+                    CK(cudaMemcpyAsync(zk.v.p, F.r.v.p, fbytes32, cudaMemcpyDeviceToDevice, s));
+                }
+                // w_k = Dhat z_k, orthogonalised against w_0..w_{k-1} (classical
+                // Gram-Schmidt, one pass: <w_j, w_k> for all j in one kernel)
+                apply32(zk, wk);
+                if (k > 0) {
+                    CK(launch_multidot32(bl, k, wp, wk.ptr(), F.mdot.as<double>(), F.dots.as<double2>(), s));
+                    launches += 2;
+                    read_dots(k);
+                    for (int j = 0; j < k; ++j)
+                        for (int i = 0; i < n; ++i) {
+                            const double d = nw[(size_t)j * n + i];
+                            const double2 v = hd[(size_t)j * n + i];
+                            hc[(size_t)j * n + i] = (d > 0) ? make_double2(-v.x / d, -v.y / d) : make_double2(0, 0);
+                        }
+                    axpy(wp, k, wk);
+                    axpy(zp, k, zk);
+                }
+                // |w_k|^2 and <w_k, r> in one pass over w_k: <r, w_k>^* = <w_k, r>
+                {
+                    const float4* const* ab = wp + k;   // a_0 = w_k
+                    CK(launch_multidot32(bl, 1, ab, wk.ptr(), F.mdot.as<double>(), F.dots.as<double2>(), s));
+                    CK(launch_multidot32(bl, 1, F.rptr.as<const float4*>(), wk.ptr(), F.mdot.as<double>(),
+                                         F.dots.as<double2>() + n, s));
+                    launches += 4;
+                }
+                read_dots(2);
+                for (int i = 0; i < n; ++i) hd[n + i].y = -hd[n + i].y;   // <r, w_k> -> <w_k, r>
+                if (use_cnn) CK(cnn_check(cnn));
+                for (int i = 0; i < n; ++i) {
+                    const double d = hd[i].x;
+                    nw[(size_t)k * n + i] = d;
+                    const double2 v = hd[n + i];
+                    hc[i] = (!done[i] && d > 0) ? make_double2(v.x / d, v.y / d) : make_double2(0, 0);
+                }
+                axpy(zp + k, 1, F.e);
+                for (int i = 0; i < n; ++i) hc[i] = make_double2(-hc[i].x, -hc[i].y);
+                axpy(wp + k, 1, F.r);
+                CK(launch_multidot32(bl, 1, F.rptr.as<const float4*>(), F.r.ptr(), F.mdot.as<double>(),
+                                     F.dots.as<double2>(), s));
+                launches += 2;
+                read_dots(1);
+                for (int i = 0; i < n; ++i) {
+                    if (done[i]) continue;
+                    rin[i] = hd[i].x;
+                    iters[i] += 1;
+                    if (!(rin[i] > target[i] * target[i])) done[i] = 1;
+                }
+                ++total;
+            }
+        }
+        // x += |r| e, then the FP64 true residual
+        for (int i = 0; i < n; ++i) sc[i] = (sweeps[i] > 0 && sc[i] > 0) ? 1.0 / sc[i] : 0.0;
+        set_scale(sc);
+        CK(launch_add32to64(bl, F.e.ptr(), F.scale.as<double>(), x.ptr(), s));
+        launches += 1;
+        residual64(dag, phi, x, s);
+        CK(cudaMemcpyAsync(rr.data(), nrm_rr.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    Result res;
+    res.sweeps = sweeps;
+    res.inner = iters;
+    res.resid.resize(n);
+    bool ok = true;
+    for (int i = 0; i < n; ++i) {
+        res.resid[i] = bb[i] > 0 ? sqrt(rr[i] / bb[i]) : 0.0;
+        if (!(rr[i] <= tol * tol * bb[i])) ok = false;
     }
     if (ok) return res;
     Result fb = solve(1, dag, phi, x, tol, maxiter, /*from_x=*/true);
@@ -1829,6 +2062,8 @@ int algo_index(sf_algo a) {
         case SF_SOLVE_CG_NORMAL: return 5;
         case SF_SOLVE_GL_BICGSTAB: return 6;
         case SF_SOLVE_BL_BICGSTAB: return 7;
+        case SF_SOLVE_FGCR_CNN_MIXED: return 8;
+        case SF_SOLVE_FGCR_MIXED: return 9;
     }
     throw SfError{SF_EINVAL, "bad algorithm"};
 }
@@ -1846,11 +2081,12 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         const int ci = algo_index(algo);
         const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5), glb = (ci == 6), blb = (ci == 7);
+        const bool fgcr32 = (ci == 8 || ci == 9);
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.launches = 0;
         w.ensure_cfg(0);
-        if (!fgcr && !blb) w.ensure_cfg(normal || glb ? 1 : ci);
+        if (!fgcr && !blb && !fgcr32) w.ensure_cfg(normal || glb ? 1 : ci);
         cudaStream_t s = lat->stream;
         const size_t bytes = (size_t)nrhs * lat->Vh * 24 * sizeof(double);
         const LaunchCfg& pl = w.cfg[0].per_lat[0];
@@ -1860,6 +2096,7 @@ sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi
         auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol) {
             if (glb) return w.gl_bicgstab(dag, rhs, sol, tol, maxiter);
             if (blb) return w.bl_bicgstab(dag, rhs, sol, tol, maxiter);
+            if (fgcr32) return w.fgcr_mixed(ci == 8, dag, rhs, sol, tol, maxiter);
             return fgcr ? w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter) : w.solve(ci, dag, rhs, sol, tol, maxiter);
         };
         Workspace::Result rx, ry;
@@ -1969,11 +2206,12 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
         const int ci = algo_index(algo);
         const bool fgcr = (ci == 3 || ci == 4), normal = (ci == 5), glb = (ci == 6), blb = (ci == 7);
+        const bool fgcr32 = (ci == 8 || ci == 9);
         CK(cudaSetDevice(lat->device));
         Workspace& w = lattice_ws(lat, nrhs);
         w.launches = 0;
         w.ensure_cfg(0);
-        if (!fgcr && !blb) w.ensure_cfg(normal || glb ? 1 : ci);
+        if (!fgcr && !blb && !fgcr32) w.ensure_cfg(normal || glb ? 1 : ci);
         ensure_odd(w);
         cudaStream_t s = lat->stream;
         const KrylovOps& o = ops_f64();
@@ -1984,10 +2222,11 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         w.launches += 1;
         // X = Dhat^-1 phi and its odd part; Y = Dhat^-dag X and its odd part
         auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol, FieldBuf& odd) {
-            if (!fgcr && !glb && !blb) return w.solve(ci, dag, rhs, sol, tol, maxiter, false, &odd);
-            Workspace::Result r = glb   ? w.gl_bicgstab(dag, rhs, sol, tol, maxiter)
-                                  : blb ? w.bl_bicgstab(dag, rhs, sol, tol, maxiter)
-                                        : w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter);
+            if (!fgcr && !glb && !blb && ci < 8) return w.solve(ci, dag, rhs, sol, tol, maxiter, false, &odd);
+            Workspace::Result r = glb     ? w.gl_bicgstab(dag, rhs, sol, tol, maxiter)
+                                  : blb   ? w.bl_bicgstab(dag, rhs, sol, tol, maxiter)
+                                  : ci >= 8 ? w.fgcr_mixed(ci == 8, dag, rhs, sol, tol, maxiter)
+                                            : w.fgcr(ci == 3, dag, rhs, sol, tol, maxiter);
             CK(o.hop(w.cfg[0].lc, 1, dag, sol.ptr(), odd.ptr(), 1.0, 1, nullptr, s));
             w.launches += 1;
             return r;
@@ -2353,6 +2592,7 @@ sf_status sf_cnn_forward(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double* r
         CK(ops_f64().unpack(pl, w.x64.ptr(), dout, s));
         finish_out(out, dout, bytes, s);
         CK(cudaStreamSynchronize(s));
+        CK(cnn_check(cnn));
     });
 }
 
@@ -2397,6 +2637,7 @@ static void cnn_grad_common(sf_cnn* cnn, sf_lattice* lat, int nrhs, const double
     std::vector<double> res2(nrhs);
     CK(cudaMemcpyAsync(res2.data(), w.nrm_rr.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    CK(cnn_check(cnn));
     double l = 0.0;
     for (int i = 0; i < nrhs; ++i) {
         l += res2[i] / r2[i] / nrhs;

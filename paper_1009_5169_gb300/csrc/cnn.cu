@@ -1,7 +1,9 @@
 // cnn.cu -- the learned preconditioner: a 4-layer 3^4-stencil convolutional
 // network on the full SF fermion lattice, trained and applied with
-// hand-written BF16 tensor-core kernels (mma.sync m16n8k16, FP32
-// accumulation), used as the preconditioner M of flexible GCR.
+// hand-written BF16 tensor-core kernels with FP32 accumulation -- the
+// convolutions on tcgen05 (conv_tc.cu) where the layer shape fits its shared
+// memory (hidden width 16), mma.sync m16n8k16 (k_conv below) otherwise and
+// for the weight gradients -- used as the preconditioner M of flexible GCR.
 //
 // Network (widths 32 -> H -> H -> H -> 24, H = 16 or 32):
 //   input   channels 0..23: the even-site residual r/s, s = |r|/sqrt(24 V/2)
@@ -27,6 +29,7 @@
 #include <string>
 #include <vector>
 
+#include "conv_tc.h"
 #include "krylov_impl.cuh"
 #include "sf_lattice.h"
 
@@ -324,12 +327,30 @@ __global__ void k_bgrad_reduce(int nblk, int CO_, const float* __restrict__ part
 }
 
 // ------------------------------------------------------------ features / output
+// The link features of every fermion site, once per network application:
+// LF[s][2 mu], LF[s][2 mu + 1] = Re, Im tr U_mu(x) / 3 (BF16, 16 bytes a site).
+__global__ void k_link_features(Geo g, const double2* __restrict__ canon, __nv_bfloat16* __restrict__ LF) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < g.V; s += (long long)gridDim.x * blockDim.x) {
+        const long long gi = s + (long long)g.L * g.L * g.L;  // gauge site of the fermion site
+        __align__(16) __nv_bfloat16 out[8];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const double2* U = canon + (gi * 4 + mu) * 9;
+            const double2 a = __ldg(U), bb = __ldg(U + 4), c = __ldg(U + 8);
+            out[2 * mu] = __float2bfloat16((float)((a.x + bb.x + c.x) / 3.0));
+            out[2 * mu + 1] = __float2bfloat16((float)((a.y + bb.y + c.y) / 3.0));
+        }
+        *reinterpret_cast<uint4*>(LF + s * 8) = *reinterpret_cast<const uint4*>(out);
+    }
+}
+
 // Input features of the network batch of 2 nrhs entries: entry b < nrhs is
 // r_b / s_b, entry nrhs + b is -r_b / s_b (s_b the RMS scale of r_b, passed as
-// inv_scale = 1 / s_b), residual channels on the even sites, link features on
-// every site.  g.nb = 2 nrhs.
-__global__ void k_features(LatDev gl, Geo g, CField<P64> r, const double* __restrict__ inv_scale,
-                           const double2* __restrict__ canon, __nv_bfloat16* __restrict__ X) {
+// inv_scale = 1 / s_b), residual channels on the even sites, the link
+// features LF on every site.  g.nb = 2 nrhs.
+template <typename P>
+__global__ void k_features(LatDev gl, Geo g, CField<P> r, const double* __restrict__ inv_scale,
+                           const __nv_bfloat16* __restrict__ LF, __nv_bfloat16* __restrict__ X) {
     const long long n = (long long)g.nb * g.V;
     const int nrhs = g.nb / 2;
     for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < n;
@@ -339,40 +360,35 @@ __global__ void k_features(LatDev gl, Geo g, CField<P64> r, const double* __rest
         int x[4];
         site_coords(g, s, x);
         const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
-        __align__(16) __nv_bfloat16 out[CIN0];
+        __align__(16) __nv_bfloat16 out[24];
         if (par == 0) {
             const int cb = s >> 1;
             const double sc = (b2 < nrhs ? 1.0 : -1.0) * inv_scale[b];
-            const long long base = (gl.soff + (long long)b * gl.Vpad) * 12;
+            cpx<typename P::real> p[4][3];
+            load_spinor<P, typename P::real>(r, vbase<P>(gl, b), gl.Vpad, cb, 0, p);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                const double2 v = __ldg(r.v + base + (long long)c * gl.Vpad + cb);
-                out[2 * c] = __float2bfloat16((float)(v.x * sc));
-                out[2 * c + 1] = __float2bfloat16((float)(v.y * sc));
+                out[2 * c] = __float2bfloat16((float)((double)p[c / 3][c % 3].re * sc));
+                out[2 * c + 1] = __float2bfloat16((float)((double)p[c / 3][c % 3].im * sc));
             }
         } else {
 #pragma unroll
             for (int c = 0; c < 24; ++c) out[c] = __float2bfloat16(0.f);
         }
-        const long long gi = (long long)s + (long long)g.L * g.L * g.L;  // gauge site of the fermion site
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            const double2* U = canon + (gi * 4 + mu) * 9;
-            const double2 a = __ldg(U), bb = __ldg(U + 4), c = __ldg(U + 8);
-            out[24 + 2 * mu] = __float2bfloat16((float)((a.x + bb.x + c.x) / 3.0));
-            out[25 + 2 * mu] = __float2bfloat16((float)((a.y + bb.y + c.y) / 3.0));
-        }
         uint4* dst = reinterpret_cast<uint4*>(X + row * CIN0);
         const uint4* srcv = reinterpret_cast<const uint4*>(out);
 #pragma unroll
-        for (int q = 0; q < CIN0 / 8; ++q) dst[q] = srcv[q];
+        for (int q = 0; q < 3; ++q) dst[q] = srcv[q];
+        dst[3] = __ldg(reinterpret_cast<const uint4*>(LF + (long long)s * 8));
     }
 }
 
 // z = r + s_b (out_b - out_{nrhs+b}) / 2 on the even sites (out FP32
-// [2 nrhs][V][24]); g.nb = 2 nrhs
+// [2 nrhs][V][24]); g.nb = 2 nrhs; r and z FP64 or FP32 blocks
+template <typename P>
 __global__ void k_output(LatDev gl, Geo g, const float* __restrict__ Y, const double* __restrict__ scale,
-                         CField<P64> r, Field<P64> z) {
+                         CField<P> r, Field<P> z) {
+    using R = typename P::real;
     const int nrhs = g.nb / 2;
     const long long n = (long long)nrhs * gl.Vh;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -382,14 +398,15 @@ __global__ void k_output(LatDev gl, Geo g, const float* __restrict__ Y, const do
         const float* yp = Y + ((long long)b * g.V + sx.lex) * COUT;
         const float* ym = Y + ((long long)(nrhs + b) * g.V + sx.lex) * COUT;
         const double sc = 0.5 * scale[b];
-        const long long base = (gl.soff + (long long)b * gl.Vpad) * 12;
+        cpx<R> p[4][3];
+        load_spinor<P, R>(r, vbase<P>(gl, b), gl.Vpad, cb, 0, p);
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-            const long long idx = base + (long long)c * gl.Vpad + cb;
-            const double2 rv = __ldg(r.v + idx);
-            z.v[idx] = make_double2(rv.x + sc * ((double)yp[2 * c] - (double)ym[2 * c]),
-                                    rv.y + sc * ((double)yp[2 * c + 1] - (double)ym[2 * c + 1]));
+            cpx<R>& q = p[c / 3][c % 3];
+            q = cpx<R>{(R)((double)q.re + sc * ((double)yp[2 * c] - (double)ym[2 * c])),
+                       (R)((double)q.im + sc * ((double)yp[2 * c + 1] - (double)ym[2 * c + 1]))};
         }
+        store_spinor<P, R>(z, vbase<P>(gl, b), gl.Vpad, cb, 0, p);
     }
 }
 
@@ -546,13 +563,15 @@ using namespace sfcnn;
 
 struct sf_cnn {
     int hidden = 32, device = 0;
+    int conv_impl = 0;    // 0: tcgen05 convolutions where the shape fits, 1: mma.sync everywhere
+    int sm_count = 152;
     cudaStream_t stream = nullptr;
     std::vector<LayerShape> layers;
     size_t nparams = 0;
     Buf params, grad, m1, m2, wf, wb;
     long long step = 0;
     // activations for a given geometry
-    Buf act[4], out, dz[2], partial, wpart, lpart;
+    Buf act[4], out, dz[2], partial, wpart, lpart, lfeat;
     Geo geo{};
     size_t wf_off[4] = {0, 0, 0, 0};
 };
@@ -577,8 +596,13 @@ void conv_launch(const Geo& g, const __nv_bfloat16* X, const __nv_bfloat16* B, c
     k_conv<CI, CO><<<blocks, 128, 0, st>>>(g, X, B, bias, relu, mask, Yh, Yf);
 }
 
-void conv_any(int ci, int co, const Geo& g, const __nv_bfloat16* X, const __nv_bfloat16* B, const float* bias, int relu,
-              const __nv_bfloat16* mask, __nv_bfloat16* Yh, float* Yf, cudaStream_t st) {
+void conv_any(const sf_cnn* c, int ci, int co, const Geo& g, const __nv_bfloat16* X, const __nv_bfloat16* B,
+              const float* bias, int relu, const __nv_bfloat16* mask, __nv_bfloat16* Yh, float* Yf, cudaStream_t st) {
+    if (c->conv_impl == 0 && conv_tc_supported(ci, co) &&
+        conv_tc(ConvTcGeo{g.L, g.T, g.V, g.nb}, ci, co, X, B, bias, relu, mask, Yh, Yf, c->sm_count, st) ==
+            cudaSuccess)
+        return;
+    cudaGetLastError();   // a geometry the tensor-core kernel does not take: mma.sync
 #define SFC(A, B_) if (ci == A && co == B_) { conv_launch<A, B_>(g, X, B, bias, relu, mask, Yh, Yf, st); return; }
     SFC(32, 32) SFC(32, 16) SFC(16, 16) SFC(16, 24) SFC(32, 24) SFC(24, 16) SFC(24, 32) SFC(16, 32)
 #undef SFC
@@ -600,6 +624,7 @@ void ensure_geo(sf_cnn* c, const Geo& g) {
     const long long rows = (long long)g.nb * g.V;
     const int H = c->hidden;
     c->act[0].ensure((size_t)rows * CIN0 * 2);
+    c->lfeat.ensure((size_t)g.V * 8 * 2);
     for (int l = 1; l < 4; ++l) c->act[l].ensure((size_t)rows * H * 2);
     c->out.ensure((size_t)rows * COUT * 4);
     c->dz[0].ensure((size_t)rows * 32 * 2);
@@ -618,7 +643,7 @@ void forward(sf_cnn* c, const Geo& g, cudaStream_t st) {
     for (int l = 0; l < 4; ++l) {
         const LayerShape& s = c->layers[l];
         const bool last = (l == 3);
-        conv_any(s.ci, s.co, g, c->act[l].as<__nv_bfloat16>(), wf + c->wf_off[l], P + s.boff, last ? 0 : 1, nullptr,
+        conv_any(c, s.ci, s.co, g, c->act[l].as<__nv_bfloat16>(), wf + c->wf_off[l], P + s.boff, last ? 0 : 1, nullptr,
                  last ? nullptr : c->act[l + 1].as<__nv_bfloat16>(), last ? c->out.as<float>() : nullptr, st);
     }
 }
@@ -641,7 +666,7 @@ void backward_layers(sf_cnn* c, const Geo& g, __nv_bfloat16* dz, __nv_bfloat16* 
         k_bgrad_reduce<<<1, 32, 0, st>>>(bblk, s.co, c->partial.as<float>(), G + s.boff);
         if (l > 0) {
             // dZ_{l-1} = (W_l^T conv dZ_l) * (act[l] > 0)
-            conv_any(s.co, s.ci, g, dz, wb + c->wf_off[l], nullptr, 0, c->act[l].as<__nv_bfloat16>(), dz2, nullptr,
+            conv_any(c, s.co, s.ci, g, dz, wb + c->wf_off[l], nullptr, 0, c->act[l].as<__nv_bfloat16>(), dz2, nullptr,
                      st);
             std::swap(dz, dz2);
         }
@@ -680,6 +705,10 @@ sf_status sf_cnn_create(sf_cnn** out, int hidden, const float* params, int devic
         auto* c = new sf_cnn();
         c->hidden = hidden;
         c->device = device;
+        if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+            cudaGetLastError();
+            c->sm_count = 152;
+        }
         c->stream = reinterpret_cast<cudaStream_t>(stream);
         const int w[5] = {CIN0, hidden, hidden, hidden, COUT};
         size_t off = 0, woff = 0;
@@ -726,6 +755,15 @@ sf_status sf_cnn_get_params(sf_cnn* c, float* params) {
     return SF_OK;
 }
 
+sf_status sf_cnn_set_conv_impl(sf_cnn* c, int impl) {
+    if (!c || (impl != 0 && impl != 1)) {
+        sf::set_last_error("sf_cnn_set_conv_impl: NULL network or impl not 0 / 1");
+        return SF_EINVAL;
+    }
+    c->conv_impl = impl;
+    return SF_OK;
+}
+
 void sf_cnn_destroy(sf_cnn* c) {
     if (!c) return;
     cudaSetDevice(c->device);
@@ -739,8 +777,9 @@ namespace sf {
 
 // M(r) for an FP64 field f of the lattice workspace (nrhs fields), into z.
 // norms_dev: |r_b| per field (device).  Used by FGCR and sf_cnn_forward.
-cudaError_t cnn_apply_field(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, const double* norms, const double* inv_norms,
-                            FieldPtr z) {
+template <typename P>
+static cudaError_t cnn_apply_any(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, const double* norms,
+                                 const double* inv_norms, FieldPtr z) {
     using namespace sfcnn;
     Geo g{v.desc.L, v.desc.T, 2 * v.desc.Vh, 2 * v.nrhs};  // entries +r/s and -r/s
     try {
@@ -749,13 +788,26 @@ cudaError_t cnn_apply_field(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, cons
         return cudaErrorMemoryAllocation;
     }
     const long long rows = (long long)g.nb * g.V;
-    int blocks = (int)std::min<long long>((rows + 255) / 256, 4 * 152);
-    k_features<<<blocks, 256, 0, v.stream>>>(v.desc, g, cf<P64>(r), inv_norms,
-                                              reinterpret_cast<const double2*>(v.canon), c->act[0].as<__nv_bfloat16>());
+    int blocks = (int)std::min<long long>((g.V + 255) / 256, 4 * c->sm_count);
+    k_link_features<<<blocks, 256, 0, v.stream>>>(g, reinterpret_cast<const double2*>(v.canon),
+                                                  c->lfeat.as<__nv_bfloat16>());
+    blocks = (int)std::min<long long>((rows + 255) / 256, 8 * c->sm_count);
+    k_features<P><<<blocks, 256, 0, v.stream>>>(v.desc, g, cf<P>(r), inv_norms, c->lfeat.as<__nv_bfloat16>(),
+                                                 c->act[0].as<__nv_bfloat16>());
     forward(c, g, v.stream);
-    blocks = (int)std::min<long long>(((long long)v.nrhs * v.desc.Vh + 255) / 256, 4 * 152);
-    k_output<<<blocks, 256, 0, v.stream>>>(v.desc, g, c->out.as<float>(), norms, cf<P64>(r), wf<P64>(z));
+    blocks = (int)std::min<long long>(((long long)v.nrhs * v.desc.Vh + 255) / 256, 8 * c->sm_count);
+    k_output<P><<<blocks, 256, 0, v.stream>>>(v.desc, g, c->out.as<float>(), norms, cf<P>(r), wf<P>(z));
     return cudaGetLastError();
+}
+
+cudaError_t cnn_apply_field(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, const double* norms, const double* inv_norms,
+                            FieldPtr z) {
+    return cnn_apply_any<P64>(c, v, r, norms, inv_norms, z);
+}
+
+cudaError_t cnn_apply_field32(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, const double* norms,
+                              const double* inv_norms, FieldPtr z) {
+    return cnn_apply_any<P32>(c, v, r, norms, inv_norms, z);
 }
 
 // forward + loss + backward; grads into c->grad; loss value into *loss (host)
@@ -770,8 +822,10 @@ cudaError_t cnn_loss_grad(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, FieldP
     }
     cudaStream_t st = v.stream;
     const long long rows = (long long)g.nb * g.V;
-    int blocks = (int)std::min<long long>((rows + 255) / 256, 4 * 152);
-    k_features<<<blocks, 256, 0, st>>>(v.desc, g, cf<P64>(r), inv_norms, reinterpret_cast<const double2*>(v.canon),
+    int blocks = (int)std::min<long long>((g.V + 255) / 256, 4 * c->sm_count);
+    k_link_features<<<blocks, 256, 0, st>>>(g, reinterpret_cast<const double2*>(v.canon), c->lfeat.as<__nv_bfloat16>());
+    blocks = (int)std::min<long long>((rows + 255) / 256, 8 * c->sm_count);
+    k_features<P64><<<blocks, 256, 0, st>>>(v.desc, g, cf<P64>(r), inv_norms, c->lfeat.as<__nv_bfloat16>(),
                                         c->act[0].as<__nv_bfloat16>());
     forward(c, g, st);
     const int lblk = (int)std::min<long long>((g.V + 255) / 256, 1024);
@@ -822,6 +876,10 @@ cudaError_t cnn_adam(sf_cnn* c, float lr, cudaStream_t st) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return refresh_bf16(c, st);
+}
+
+cudaError_t cnn_check(sf_cnn*) {
+    return sfcnn::conv_tc_error(true) ? cudaErrorLaunchTimeout : cudaSuccess;
 }
 
 cudaError_t cnn_copy_grad(sf_cnn* c, float* out, cudaStream_t st) {

@@ -215,4 +215,25 @@ cudaError_t cnn_loss_grad(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, FieldP
 cudaError_t cnn_backward_field(sf_cnn* c, const CnnLatticeView& v, FieldPtr G, const double* coef);
 cudaError_t cnn_adam(sf_cnn* c, float lr, cudaStream_t st);
 cudaError_t cnn_copy_grad(sf_cnn* c, float* out, cudaStream_t st);
+// FP32 vector kernels of the mixed-precision flexible GCR (fgcr32.cu), on
+// the FP64 BLAS tiling: <a_i, b_i> per (lattice, rhs) into out (device,
+// float-float partial sums, fixed-order lattice sums), y_i += sum_j c[j][i]
+// x_j, gamma_5, and the conversions r32 = scale r64, x64 += scale e32.
+cudaError_t launch_dot32(const LaunchCfg& c, FieldPtr a, FieldPtr b, const SolverCtx* ctx, double2* out,
+                         cudaStream_t st);
+cudaError_t launch_multi_axpy32(const LaunchCfg& c, int nvec, const float4* const* xs, const double2* coef, FieldPtr y,
+                                cudaStream_t st);
+cudaError_t launch_gamma5_32(long long nplanes, int Vpad, FieldPtr in, FieldPtr out, int sm_count, cudaStream_t st);
+cudaError_t launch_to32(const LaunchCfg& c, FieldPtr in, const double* scale, FieldPtr out, cudaStream_t st);
+cudaError_t launch_add32to64(const LaunchCfg& c, FieldPtr e, const double* scale, FieldPtr x, cudaStream_t st);
+// out[j nrhs + i] = <a_j, b_i> for j < nvec (<= 18) on one lattice in one pass
+// over b; partials: 2 nvec nrhs c.nblocks doubles of scratch
+cudaError_t launch_multidot32(const LaunchCfg& c, int nvec, const float4* const* as, FieldPtr b, double* partials,
+                              double2* out, cudaStream_t st);
+// the network's M(r) for an FP32 field (as cnn_apply_field)
+cudaError_t cnn_apply_field32(sf_cnn* c, const CnnLatticeView& v, FieldPtr r, const double* norms,
+                              const double* inv_norms, FieldPtr z);
+// after a synchronisation: cudaErrorLaunchTimeout if a tensor-core
+// convolution's wait timed out since the last check (clears the flag)
+cudaError_t cnn_check(sf_cnn* c);
 }  // namespace sf

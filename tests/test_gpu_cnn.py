@@ -186,5 +186,46 @@ def test_training_and_fgcr_gain(sf):
     print(f"FGCR iterations X/Y: learned {i_cnn['iters_inner']}/{i_cnn['iters_inner_y']}, "
           f"identity {i_id['iters_inner']}/{i_id['iters_inner_y']}")
     assert i_cnn["iters_inner"] < i_id["iters_inner"], (i_cnn, i_id)
+    # the mixed-precision form: FP32 flexible GCR under FP64 defect correction
+    res = {}
+    for algo in ("fgcr_cnn_mixed", "fgcr_mixed"):
+        X, Y = np.empty_like(phi), np.empty_like(phi)
+        res[algo] = sf.solve_block(lat, algo, phi, X, Y, tol=1e-10, maxiter=2000)
+        rx = oracle.true_residual(U, phi, X, L, T, lt.theta, lt.kappa)
+        ry = oracle.true_residual(U, X, Y, L, T, lt.theta, lt.kappa, dagger=True)
+        assert np.all(rx <= 1.05e-10) and np.all(ry <= 1.05e-10), (algo, rx, ry)
+        assert np.max(np.abs(X - X1)) <= 1e-7 * np.max(np.abs(X1)), algo   # the same solution as the FP64 FGCR
+    print(f"mixed FGCR iterations X/Y: learned {res['fgcr_cnn_mixed']['iters_inner']}/"
+          f"{res['fgcr_cnn_mixed']['iters_inner_y']}, identity {res['fgcr_mixed']['iters_inner']}/"
+          f"{res['fgcr_mixed']['iters_inner_y']}")
+    assert res["fgcr_cnn_mixed"]["iters_inner"] < res["fgcr_mixed"]["iters_inner"], res
     lat.close()
     net.close()
+
+
+@pytest.mark.parametrize("L,T", [(4, 6), (6, 5), (8, 8), (12, 4), (16, 3)])
+def test_tcgen05_convolutions_match_mma_sync(sf, L, T):
+    """The tcgen05 convolutions (tiles of 16 x2-lines by 8 x3-sites, padded
+    and wrapped at L = 4, 6, 12) against the mma.sync kernel on the same
+    network: forward output and the parameter gradients (whose backward-data
+    convolutions also run on tcgen05).  Both accumulate the same BF16
+    products in FP32 in different orders, so the difference is at BF16
+    rounding of the intermediate activations."""
+    U = inputs.links(L, T, 0.3, 401 + L)
+    r = inputs.sources(L, T, 3, 402 + L)
+    e = inputs.sources(L, T, 3, 403 + L)
+    p = inputs.cnn_init_params(16, 404, last_scale=1.0)
+    p[-24:] = 0.05 * np.arange(24) / 24
+    lat = sf.Lattice(L, T, 0.5, 0.13, 4.52, U)
+    outs, grads = {}, {}
+    for impl in ("mma_sync", "tcgen05"):
+        net = sf.Cnn(16, p)
+        net.set_conv_impl(impl)
+        out = np.empty_like(r)
+        net.forward(lat, r, out)
+        outs[impl] = out
+        grads[impl] = net.gradients(lat, r, e)[0]
+        net.close()
+    lat.close()
+    assert frob(outs["tcgen05"], outs["mma_sync"]) <= 5e-3, frob(outs["tcgen05"], outs["mma_sync"])
+    assert frob(grads["tcgen05"], grads["mma_sync"]) <= 2e-2, frob(grads["tcgen05"], grads["mma_sync"])

@@ -193,7 +193,8 @@ def test_solve_five_rhs_and_force_sf12(sf):
     lat.close()
 
 
-@pytest.mark.parametrize("algo", ["mixed_dc", "bicgstab", "fgcr", "cg_normal", "gl_bicgstab", "bl_bicgstab"])
+@pytest.mark.parametrize("algo", ["mixed_dc", "bicgstab", "fgcr", "cg_normal", "gl_bicgstab", "bl_bicgstab",
+                                  "fgcr_mixed"])
 def test_md_force_step_matches_separate_calls(sf, algo):
     """Alg. 2 in one call reuses the odd-site hops of the final residuals: the
     same X, Y and force, bitwise, as solve_block followed by fermion_force
@@ -365,7 +366,8 @@ def test_block_solvers_refuse_more_than_eight_rhs(sf):
     lat.close()
 
 
-@pytest.mark.parametrize("algo", ["mixed_dc", "cg_normal", "bicgstab", "gl_bicgstab", "bl_bicgstab", "fgcr"])
+@pytest.mark.parametrize("algo", ["mixed_dc", "cg_normal", "bicgstab", "gl_bicgstab", "bl_bicgstab", "fgcr",
+                                  "fgcr_mixed"])
 def test_zero_sources(sf, algo):
     """phi = 0 (the degenerate block): X = Y = 0 exactly, status OK."""
     L, T = 4, 5
