@@ -53,10 +53,10 @@ namespace sfcnn {
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;   // warp 0: MMA issue; warps 1-7: slice fetches; warps 4-7: epilogue
 constexpr int BOX_X3 = 10;      // 8 sites + halo
 constexpr int BOX_LINES = 18;   // 16 lines + halo
-constexpr int SLOTS = 3;        // the input slice in use and the next two
+constexpr int SLOTS = 4;        // the slices of the MMAs in flight and the next two
 constexpr int PLANE = BOX_LINES * BOX_X3;          // entries of one x1 plane of the box
 constexpr int KC_STRIDE = 3 * PLANE;               // entries between channel chunks
 constexpr int CB = 16;                             // output channels per unit (one TMEM block)
@@ -179,15 +179,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ Yh, float* __restrict__ Yf) {
     constexpr int KC = CIP / 8;                     // 16-byte channel chunks
     constexpr int SLOT_ENTRIES = KC * KC_STRIDE;    // one input slice box
+    constexpr int NLOAD = TC_THREADS - 32;          // fetching threads (warps 1-7)
     extern __shared__ __align__(128) uint4 smem[];
+    __shared__ int s_abort;
     const int nblk_c = (CO + CB - 1) / CB;          // 16-channel blocks of the output
     const int w_entries = nblk_c * 27 * KC * NB;
     uint4* box = smem;
     uint4* wsm = smem + SLOTS * SLOT_ENTRIES;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(wsm + w_entries);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(wsm + w_entries);   // [2]: commits of even / odd slices
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool issuer = (tid == 0), loader = (warp >= 1), epi = (warp >= 4);
+    const int ltid = tid - 32;                      // index among the fetching threads
     const int L = g.L, T = g.T;
     const int n_x2t = (L + 15) / 16, n_x3b = (L + 7) / 8;
     const long long units = (long long)g.nb * L * n_x2t * n_x3b * nblk_c;
@@ -202,7 +206,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         wsm[e] = v;
     }
     if (tid == 0) {
+        s_abort = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + 1)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -216,20 +222,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;   // output slice o of the unit: columns tmem + 16 o, o = 0..T
-    const uint32_t box_a = smem_u32(box), w_a = smem_u32(wsm), mbar_a = smem_u32(mbar);
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    uint32_t phase = 0;
-    bool ok = true;
+    const uint32_t box_a = smem_u32(box), w_a = smem_u32(wsm);
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;   // this warp's tensor-memory lane quarter
+    uint32_t phase[2] = {0u, 0u};
 
-    // This thread's entries of a slice fetch (e = tid + 128 j): source element
-    // offset without the x0 term and box entry without the slot term, per unit.
-    constexpr int NE = (SLOT_ENTRIES + TC_THREADS - 1) / TC_THREADS;
+    // This thread's entries of a slice fetch (e = ltid + NLOAD j): source
+    // element offset without the x0 term and box entry, set per unit.
+    constexpr int NE = (SLOT_ENTRIES + NLOAD - 1) / NLOAD;
     int src_off[NE], dst_off[NE];
     const int x0_stride = L * L * L * CI;   // elements between time slices
     auto set_unit = [&](int b, int x1, int x2_0, int x3_0) {
 #pragma unroll
         for (int j = 0; j < NE; ++j) {
-            const int e = tid + j * TC_THREADS;
+            const int e = ltid + j * NLOAD;
             dst_off[j] = -1;
             src_off[j] = -1;
             if (e >= SLOT_ENTRIES) continue;
@@ -241,8 +246,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     };
-    auto load_slice = [&](int x0, int slot) {
-        const int xoff = (x0 - 1) * x0_stride, soff = slot * SLOT_ENTRIES;
+    // fetching threads: input slice x0 into ring slot (x0 - 1) % 4
+    auto load_slice = [&](int x0) {
+        const int xoff = (x0 - 1) * x0_stride, soff = ((x0 - 1) % SLOTS) * SLOT_ENTRIES;
 #pragma unroll
         for (int j = 0; j < NE; ++j) {
             if (dst_off[j] < 0) continue;
@@ -251,22 +257,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         cp_async_commit();
     };
-    // wait for the MMAs committed last; the block leaves together if a wait timed out
-    auto wait_mma = [&]() -> bool {
-        const bool w = mbar_wait(mbar_a, phase);
-        if (!__syncthreads_and(w ? 1 : 0)) {
-            if (tid == 0) atomicExch(&g_conv_tc_error, 1);
-            return false;
+    // wait for the commit of slice x0's MMAs (no barrier: the issuing warp keeps issuing);
+    // a timeout raises the abort flag, which every thread reads after the next barrier
+    auto wait_slice = [&](int x0) {
+        const int m = x0 & 1;
+        if (!mbar_wait(smem_u32(mbar + m), phase[m])) {
+            s_abort = 1;
+            atomicExch(&g_conv_tc_error, 1);
         }
-        phase ^= 1u;
+        phase[m] ^= 1u;
         tc_fence_after();
-        return true;
     };
-    // write output slice o (complete) of the unit: this thread's row
+    // write output slice o (complete) of the unit: this thread's row (epilogue warps)
     auto epilogue = [&](int o, int b, int x1, int x2_0, int x3_0, int cb) {
         float v[CB];
         tmem_load_row<CB>(tmem + (uint32_t)(CB * o) + lane_base, v);
-        const int row = warp * 32 + lane;   // line (row >> 3), site (row & 7)
+        const int row = (warp & 3) * 32 + lane;   // line (row >> 3), site (row & 7)
         const int x2 = x2_0 + (row >> 3), x3 = x3_0 + (row & 7);
         if (x2 >= L || x3 >= L) return;
         const long long orow = (long long)b * g.V + ((((long long)(o - 1) * L + x1) * L + x2) * L + x3);
@@ -293,6 +299,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     };
 
+    bool ok = true;
     for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
         long long r = u;
         const int cb = (int)(r % nblk_c); r /= nblk_c;
@@ -301,11 +308,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int x1 = (int)(r % L); r /= L;
         const int b = (int)r;
         const int x2_0 = x2t * 16, x3_0 = x3b * 8;
-        set_unit(b, x1, x2_0, x3_0);
-        load_slice(1, 0);
-        if (T - 1 >= 2) load_slice(2, 1);
-        // zero this warp's lanes of the T + 1 output slices (the MMAs only accumulate)
-        {
+        if (loader) {
+            set_unit(b, x1, x2_0, x3_0);
+            load_slice(1);
+            if (T - 1 >= 2) load_slice(2);
+        }
+        if (epi) {   // zero this warp's lanes of the T + 1 output slices (the MMAs only accumulate)
             uint32_t z[CB];
 #pragma unroll
             for (int c = 0; c < CB; ++c) z[c] = 0u;
@@ -320,30 +328,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         const uint64_t b0 = sdesc(w_a + (uint32_t)(cb * 27 * KC * NB) * 16u, NB * 16, 128);
         for (int x0 = 1; x0 <= T - 1; ++x0) {
-            const int slot = (x0 - 1) % SLOTS;
-            // input slice x0 (fetched two slices ahead); slice x0 + 1 may still be in flight
-            if (x0 + 1 <= T - 1) cp_async_wait_prev();
-            else cp_async_wait_all();
+            if (loader) {   // this thread's part of slice x0 (slice x0 + 1 may still be in flight)
+                if (x0 + 1 <= T - 1) cp_async_wait_prev();
+                else cp_async_wait_all();
+            }
             fence_proxy_async();
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
-            if (x0 >= 2 && !(ok = wait_mma())) break;   // slice x0 - 1's MMAs
-            if (x0 + 2 <= T - 1) load_slice(x0 + 2, (x0 + 1) % SLOTS);   // the slot slice x0 - 1 used
-            if (tid == 0) {
-                const uint64_t a0 = sdesc(box_a + (uint32_t)(slot * SLOT_ENTRIES) * 16u, KC_STRIDE * 16, BOX_X3 * 16);
-                issue_all<KC>(tmem + (uint32_t)(CB * (x0 - 1)), a0, b0, std::make_integer_sequence<int, 27>{});
-                mma_commit(mbar_a);
+            if (s_abort) {
+                ok = false;
+                break;
             }
-            if (x0 >= 3) epilogue(x0 - 2, b, x1, x2_0, x3_0, cb);   // complete since slice x0 - 1
+            if (issuer) {
+                const uint64_t a0 = sdesc(box_a + (uint32_t)(((x0 - 1) % SLOTS) * SLOT_ENTRIES) * 16u,
+                                          KC_STRIDE * 16, BOX_X3 * 16);
+                issue_all<KC>(tmem + (uint32_t)(CB * (x0 - 1)), a0, b0, std::make_integer_sequence<int, 27>{});
+                mma_commit(smem_u32(mbar + (x0 & 1)));
+            }
+            if (warp >= 1 && x0 >= 2) {
+                wait_slice(x0 - 1);   // then slice x0 - 2's slot is free and output x0 - 2 complete
+                if (x0 + 2 <= T - 1) load_slice(x0 + 2);
+                if (epi && x0 >= 3) epilogue(x0 - 2, b, x1, x2_0, x3_0, cb);
+            } else if (loader && x0 + 2 <= T - 1) {
+                load_slice(x0 + 2);   // x0 = 1: slot 3 is unused yet
+            }
         }
-        if (!ok) break;
-        if (!(ok = wait_mma())) break;
-        if (T - 2 >= 1) epilogue(T - 2, b, x1, x2_0, x3_0, cb);
-        epilogue(T - 1, b, x1, x2_0, x3_0, cb);
+        // the unit's last slice: its MMAs, then outputs T - 2 and T - 1
+        __syncthreads();
+        if (!ok || s_abort) {
+            ok = false;
+            break;
+        }
+        if (warp >= 1) {
+            wait_slice(T - 1);
+            if (epi) {
+                if (T - 2 >= 1) epilogue(T - 2, b, x1, x2_0, x3_0, cb);
+                epilogue(T - 1, b, x1, x2_0, x3_0, cb);
+            }
+        } else {
+            phase[(T - 1) & 1] ^= 1u;   // the issuing warp's view of the same phase
+        }
         tc_fence_before();
-        __syncthreads();   // every warp's reads done before the next unit zeroes the accumulators
+        __syncthreads();   // every epilogue read done before the next unit zeroes the accumulators
         tc_fence_after();
+        if (s_abort) ok = false;
     }
     // release the tensor memory (every thread's reads are complete: tcgen05.wait::ld)
     cp_async_wait_all();
@@ -357,7 +386,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 template <int CIP>
 static size_t conv_tc_smem(int co) {
     const int nblk_c = (co + CB - 1) / CB;
-    return (size_t)SLOTS * (CIP / 8) * KC_STRIDE * 16 + (size_t)nblk_c * 27 * (CIP / 8) * NB * 16 + 16;
+    return (size_t)SLOTS * (CIP / 8) * KC_STRIDE * 16 + (size_t)nblk_c * 27 * (CIP / 8) * NB * 16 + 32;
 }
 
 template <int CIP>
