@@ -66,7 +66,7 @@ def _ncu_traffic(key, TS, NR, pipe=0):
     try:
         with open(os.path.join(ROOT, "profiles", "dslash_traffic.json")) as f:
             d = json.load(f)
-        e = d.get(f"{key}:TS{TS}NR{NR}" + (":pipe" if pipe else ""))
+        e = d.get(f"{key}:TS{TS}NR{NR}" + (f":pipe{pipe}" if pipe else ""))
         if e and e.get("kernel_hash") == _kernel_hash():
             return e
     except Exception:
@@ -797,6 +797,44 @@ def run_dslash_only(args, local_rank):
     print(json.dumps({"dslash_only": f"{L}^3x{T}", "tiling": args.tiling, "reps": args.reps, **res}), flush=True)
 
 
+def run_network_only(args, local_rank):
+    """The learned preconditioner's forward pass alone on an L^4 lattice
+    with 5 RHS and seeded, untrained weights (for profiler captures): one
+    application per convolution implementation, then `reps` timed ones."""
+    import torch
+    from paper_1009_5169_gb300 import binding as sf
+    from paper_1009_5169_gb300 import inputs
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    L = args.network_lattice
+    hidden = 16
+    lt = inputs.Lattice(L, L, 0.2, 0.134, inputs.SEED_BASE + 1000)
+    lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(lt.make_links()).to(dev),
+                     device=local_rank)
+    r = torch.from_numpy(inputs.sources(lt.L, lt.T, 5, inputs.SEED_BASE + 1000)).to(dev)
+    out = torch.empty_like(r)
+    net = sf.Cnn(hidden, inputs.cnn_init_params(hidden, inputs.SEED_BASE + 40), device=local_rank)
+    stream = torch.cuda.current_stream(dev)
+    widths = inputs.cnn_widths(hidden)
+    flops = 2.0 * 81 * sum(ci * co for ci, co in zip(widths[:-1], widths[1:])) * 2 * 5 * L ** 3 * L
+    res = {}
+    for impl in args.network_impls.split(","):
+        net.set_conv_impl(impl)
+        net.forward(lat, r, out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.reps):
+            net.forward(lat, r, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) * 1e-3 / args.reps
+        res[impl] = {"forward_ms": round(t * 1e3, 3), "conv_tflops": round(flops / t / 1e12, 1)}
+    net.close()
+    lat.close()
+    print(json.dumps({"network_only": f"{L}^4", "widths": widths, "reps": args.reps, **res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -831,9 +869,16 @@ def main():
     ap.add_argument("--tiling", type=int, nargs="+", default=(64, 1), metavar="N",
                     help="TS NR [pipe]: sites per tile, rhs per thread, pipelined hop (0/1)")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--network-only", action="store_true",
+                    help="time the learned preconditioner's forward pass alone (profiling aid)")
+    ap.add_argument("--network-lattice", type=int, default=24, metavar="L")
+    ap.add_argument("--network-impls", default="tcgen05,mma_sync")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
     rank, world, local_rank = _env_rank()
+    if args.network_only:
+        run_network_only(args, local_rank)
+        return
     if args.dslash_only:
         run_dslash_only(args, local_rank)
         return
