@@ -27,6 +27,7 @@
 #include <tuple>
 #include <vector>
 
+#include "blocksolve.h"
 #include "sf_kernels.h"
 #include "sf_lattice.h"
 
@@ -254,6 +255,9 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond = 0;
     long long pro_k = 0, sweep_k = 0;   // graph-resident solve: kernels of the prologue and of one sweep
+    // block solvers: kernels of one cycle, one iteration body, its second
+    // half and one preconditioner call (without its inner iterations)
+    long long cyc_k = 0, it_k = 0, if_k = 0, call_k = 0;
     ~GraphEntry() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -301,6 +305,7 @@ struct Workspace {
     long long launches = 0;
 
     ~Workspace() {
+        blk.reset();
         graphs.clear();
         if (pin) cudaFreeHost(pin);
         solve_graphs.clear();
@@ -383,6 +388,7 @@ struct Workspace {
         // graphs bake launch shapes in
         for (int k : {0, 1, 8, 9}) graphs.erase(ci * 2 + k);
         solve_graphs.clear();
+        if (this->blk) this->blk->graphs.clear();
     }
 
     void ensure_inner(int ci) {
@@ -489,8 +495,10 @@ struct Workspace {
         }
     }
 
-    // add a WHILE node controlled by h after the work captured so far on s; returns its body graph
-    static cudaGraph_t add_while(cudaStream_t s, cudaGraphConditionalHandle h) {
+    // add a conditional node (WHILE or IF) controlled by h after the work
+    // captured so far on s; returns its body graph
+    static cudaGraph_t add_while(cudaStream_t s, cudaGraphConditionalHandle h,
+                                 cudaGraphConditionalNodeType type = cudaGraphCondTypeWhile) {
         cudaStreamCaptureStatus cs;
         cudaGraph_t g = nullptr;
         const cudaGraphNode_t* deps = nullptr;
@@ -501,12 +509,34 @@ struct Workspace {
         cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
         cp.type = cudaGraphNodeTypeConditional;
         cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.type = type;
         cp.conditional.size = 1;
         cudaGraphNode_t node;
         CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
         CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
         return cp.conditional.phGraph_out[0];
+    }
+
+    static void abandon_capture(cudaStream_t s) {
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(s, &dummy);
+        if (dummy) cudaGraphDestroy(dummy);
+    }
+
+    // a conditional node after the work captured so far on parent, its body
+    // captured on child by fn(child)
+    template <class F>
+    static void cond_body(cudaStream_t parent, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                          cudaStream_t child, F&& fn) {
+        cudaGraph_t body = add_while(parent, h, type);
+        CK(cudaStreamBeginCaptureToGraph(child, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        try {
+            fn(child);
+        } catch (...) {
+            abandon_capture(child);
+            throw;
+        }
+        CK(cudaStreamEndCapture(child, &body));
     }
 
     static cudaGraphConditionalHandle new_handle(cudaStream_t s) {
@@ -717,6 +747,37 @@ struct Workspace {
     // y_j += sum_i x_i C[i][j] (C row-major s x s, host)
     void block_axpy64(const FieldBuf& x, const std::vector<std::complex<double>>& C, FieldBuf& y);
     Result bl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
+    void ensure_gl();
+
+    // ---- the device-resident forms of both block solvers (blocksolve.cu):
+    // one graph per (solver, direction, fields, tol, maxiter), launched once
+    // per solve with one synchronisation at its end
+    struct Blk {
+        DevMem state, partials;
+        cudaStream_t cs[2] = {nullptr, nullptr};   // capture streams of the IF bodies and the inner loops
+        struct Key {
+            int gl, dag;
+            const void *phi, *x;
+            double tol;
+            int maxiter;
+            bool operator<(const Key& o) const {
+                return std::tie(gl, dag, phi, x, tol, maxiter) < std::tie(o.gl, o.dag, o.phi, o.x, o.tol, o.maxiter);
+            }
+        };
+        std::map<Key, std::unique_ptr<GraphEntry>> graphs;
+        ~Blk() {
+            graphs.clear();
+            for (cudaStream_t c : cs)
+                if (c) cudaStreamDestroy(c);
+        }
+    };
+    std::unique_ptr<Blk> blk;
+    void ensure_blk();
+    // out = M in inside a capture on s (the inner WHILE body on child)
+    void capture_precondition(bool dag, const FieldBuf& in, FieldBuf& out, int maxiter, cudaStream_t s,
+                              cudaStream_t child);
+    Result bl_bicgstab_graph(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
+    Result gl_bicgstab_graph(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter);
 
     // per-rhs |b - A x| / |b| in FP64 (A = Dhat, or Dhat^dag for dag)
     std::vector<double> rel_residual(bool dag, const FieldBuf& b, const FieldBuf& x) {
@@ -1352,6 +1413,22 @@ Workspace::Result Workspace::fgcr_mixed(bool use_cnn, bool dag, const FieldBuf& 
 }
 
 // ---------------------------------------------------------------- Gl-BiCGStab
+// the eight FP64 block vectors of Gl- and Bl-BiCGStab
+void Workspace::ensure_gl() {
+    if (gl) return;
+    gl.reset(new Gl());
+    FieldBuf* f[8] = {&gl->r, &gl->r0, &gl->p, &gl->v, &gl->s, &gl->t, &gl->ph, &gl->sh};
+    std::vector<void*> p(8);
+    for (int k = 0; k < 8; ++k) {
+        f[k]->alloc(Prec::F64, S);
+        p[k] = f[k]->v.p;
+    }
+    gl->ptrs.ensure(p.size() * sizeof(void*));
+    CK(cudaMemcpy(gl->ptrs.p, p.data(), p.size() * sizeof(void*), cudaMemcpyHostToDevice));
+    gl->coef.ensure((size_t)2 * nrhs * sizeof(double2));
+    gl->dots.ensure((size_t)nrhs * sizeof(double2));
+}
+
 // out = M in, the preconditioner of the Gl-BiCGStab outer solver: for each rhs
 // one FP32-inner BiCGStab solve of Dhat e = in_i / |in_i| (dag: Dhat^dag) from
 // e = 0 to relative residual delta, out_i = |in_i| e (the whole block in one
@@ -1422,25 +1499,15 @@ void Workspace::precondition(bool dag, const FieldBuf& in, FieldBuf& out, double
 Workspace::Result Workspace::gl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
     REQUIRE(nlat == 1, "Gl-BiCGStab runs on a single lattice");
     REQUIRE(nrhs <= 8, "FGCR, Gl-BiCGStab and Bl-BiCGStab take up to 8 right-hand sides (one 32-site row per rhs)");
+    // the device-resident form unless kernels are launched one by one (profilers)
+    if (!no_graph()) return gl_bicgstab_graph(dag, phi, x, tol, maxiter);
     ensure_cfg(0);
     ensure_cfg(1);
     ensure_cfg(3);
     cudaStream_t s = stream;
     const int n = nrhs;
     const size_t fbytes = field_bytes(Prec::F64, S);
-    if (!gl) {
-        gl.reset(new Gl());
-        FieldBuf* f[8] = {&gl->r, &gl->r0, &gl->p, &gl->v, &gl->s, &gl->t, &gl->ph, &gl->sh};
-        std::vector<void*> p(8);
-        for (int k = 0; k < 8; ++k) {
-            f[k]->alloc(Prec::F64, S);
-            p[k] = f[k]->v.p;
-        }
-        gl->ptrs.ensure(p.size() * sizeof(void*));
-        CK(cudaMemcpy(gl->ptrs.p, p.data(), p.size() * sizeof(void*), cudaMemcpyHostToDevice));
-        gl->coef.ensure((size_t)2 * n * sizeof(double2));
-        gl->dots.ensure((size_t)n * sizeof(double2));
-    }
+    ensure_gl();
     enum { kR = 0, kR0, kP, kV, kS, kT, kPH, kSH };
     const double2* const* ptr = gl->ptrs.as<const double2*>();
     const LaunchCfg& bl = cfg[3].lc;
@@ -1634,24 +1701,13 @@ void Workspace::block_axpy64(const FieldBuf& x, const std::vector<std::complex<d
 Workspace::Result Workspace::bl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
     REQUIRE(nlat == 1, "Bl-BiCGStab runs on a single lattice");
     REQUIRE(nrhs <= 8, "FGCR, Gl-BiCGStab and Bl-BiCGStab take up to 8 right-hand sides (one 32-site row per rhs)");
+    if (!no_graph()) return bl_bicgstab_graph(dag, phi, x, tol, maxiter);
     ensure_cfg(0);
     ensure_cfg(3);
     cudaStream_t s = stream;
     const int n = nrhs;
     const size_t fbytes = field_bytes(Prec::F64, S);
-    if (!gl) {
-        gl.reset(new Gl());
-        FieldBuf* f[8] = {&gl->r, &gl->r0, &gl->p, &gl->v, &gl->s, &gl->t, &gl->ph, &gl->sh};
-        std::vector<void*> p(8);
-        for (int k = 0; k < 8; ++k) {
-            f[k]->alloc(Prec::F64, S);
-            p[k] = f[k]->v.p;
-        }
-        gl->ptrs.ensure(p.size() * sizeof(void*));
-        CK(cudaMemcpy(gl->ptrs.p, p.data(), p.size() * sizeof(void*), cudaMemcpyHostToDevice));
-        gl->coef.ensure((size_t)2 * n * sizeof(double2));
-        gl->dots.ensure((size_t)n * sizeof(double2));
-    }
+    ensure_gl();
     using cd = std::complex<double>;
     std::vector<double2> hd(n);
     auto dots = [&](const FieldBuf& a, const FieldBuf& b) {
@@ -1751,6 +1807,269 @@ Workspace::Result Workspace::bl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf
         res.sweeps[i] = cycles;
         res.inner[i] = iters;
         res.resid[i] = bb[i] > 0 ? sqrt(rt[i] / bb[i]) : 0.0;
+    }
+    return res;
+}
+
+// ---------------------------------------------------------------- device-resident block solvers
+void Workspace::ensure_blk() {
+    if (!blk) {
+        blk.reset(new Blk());
+        const size_t sb = std::max(sizeof(BlState), sizeof(GlState));
+        blk->state.ensure(sb);
+        CK(cudaMemset(blk->state.p, 0, sb));
+        for (cudaStream_t& c : blk->cs) CK(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    }
+    const int nb = std::max(cfg[0].lc.nblocks, cfg[3].lc.nblocks);
+    const size_t need = (size_t)BLK_NQ_R * BLK_MAX * nb * sizeof(double);
+    if (blk->partials.bytes < need) {
+        blk->graphs.clear();   // they hold the old buffer
+        blk->partials.ensure(need);
+    }
+}
+
+// Bl-BiCGStab as one graph (the iteration of bl_bicgstab, Sec. 3.2 case C):
+//   prologue: |phi|^2, X = 0, R = phi, state start (opens the cycle loop)
+//   WHILE cycle: R0 = R, P = R, Q = R0^H R and the stop test
+//     WHILE iteration: V = A P; M = R0^H V, M = QR, alpha = M^-1 Q;
+//       S = R - V alpha with X += P alpha and |S|^2; the half-step test
+//       IF not converged: T = A S with <T, S>, |T|^2; omega; X += omega S,
+//         R = S - omega T with |R|^2, R0^H R, R0^H T; the stop test,
+//         beta = -M^-1 R0^H T
+//       P = R + (P - omega V) beta, and the iteration loop's condition
+//     FP64 true residual, another cycle while a rhs is above tol, R = r
+Workspace::Result Workspace::bl_bicgstab_graph(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
+    ensure_cfg(0);
+    ensure_cfg(3);
+    ensure_gl();
+    ensure_blk();
+    const int n = nrhs, max_cycles = 4;
+    cudaStream_t s = stream;
+    BlState* bs = blk->state.as<BlState>();
+    double* pt = blk->partials.as<double>();
+    const LaunchCfg& bl = cfg[3].lc;
+    const int nb0 = cfg[0].lc.nblocks, nb3 = bl.nblocks;
+    const long long nel = 24LL * S;   // doubles of one FP64 block vector
+    const Blk::Key key{0, dag ? 1 : 0, phi.v.p, x.v.p, tol, maxiter};
+    auto it = blk->graphs.find(key);
+    if (it == blk->graphs.end()) {
+        const KrylovOps& o64 = ops_f64();
+        const FieldPtr none{nullptr, nullptr};
+        Gl& g = *gl;
+        auto ge = std::make_unique<GraphEntry>();
+        const long long saved = launches;
+        CK(cudaStreamBeginCapture(cap_top, cudaStreamCaptureModeThreadLocal));
+        try {
+            const cudaGraphConditionalHandle h_cycle = new_handle(cap_top);
+            launches = 0;
+            SolverCtx k0 = ctx(false);
+            CK(launch_norm2(cfg[0].lc, phi.ptr(), &k0, nrm_bb.as<double>(), cap_top));
+            CK(launch_copy_f64(x.v.as<double>(), nullptr, nel, sm_count, cap_top));
+            CK(launch_copy_f64(g.r.v.as<double>(), phi.v.as<double>(), nel, sm_count, cap_top));
+            CK(launch_bl_init(bs, n, nrm_bb.as<double>(), tol, maxiter, max_cycles, h_cycle, cap_top));
+            ge->pro_k = launches + 5;
+            cond_body(cap_top, h_cycle, cudaGraphCondTypeWhile, cap_sweep, [&](cudaStream_t c1) {
+                launches = 0;
+                CK(launch_copy_f64(g.r0.v.as<double>(), g.r.v.as<double>(), nel, sm_count, c1));
+                CK(launch_copy_f64(g.p.v.as<double>(), g.r.v.as<double>(), nel, sm_count, c1));
+                CK(launch_gram64(bl, g.r0.ptr(), g.r.ptr(), pt, nullptr, c1));
+                const cudaGraphConditionalHandle h_iter = new_handle(c1);
+                CK(launch_bl_fin_q(bs, pt, nb3, h_iter, c1));
+                cond_body(c1, h_iter, cudaGraphCondTypeWhile, cap_stream, [&](cudaStream_t c2) {
+                    const long long outer = launches;
+                    launches = 0;
+                    apply_dhat64(dag, g.p, g.v, c2);
+                    CK(launch_gram64(bl, g.r0.ptr(), g.v.ptr(), pt, nullptr, c2));
+                    CK(launch_bl_fin_alpha(bs, pt, nb3, c2));
+                    CK(launch_bl_s(bl, bs, g.r.ptr(), g.v.ptr(), g.p.ptr(), g.s.ptr(), x.ptr(), pt, c2));
+                    const cudaGraphConditionalHandle h_if = new_handle(c2);
+                    CK(launch_bl_fin_s(bs, pt, nb3, h_if, c2));
+                    cond_body(c2, h_if, cudaGraphCondTypeIf, blk->cs[0], [&](cudaStream_t c3) {
+                        SolverCtx kp = ctx(false);
+                        kp.partials = pt;
+                        CK(o64.hop(cfg[0].lc, 1, dag, g.s.ptr(), t64o.ptr(), 1.0, 0, nullptr, c3));
+                        CK(o64.tail(cfg[0].lc, 0, dag, RED_TS, t64o.ptr(), g.s.ptr(), none, g.t.ptr(), none, 1.0,
+                                    -1.0, 2, &kp, nullptr, c3));
+                        CK(launch_bl_fin_omega(bs, pt, nb0, c3));
+                        CK(launch_bl_r(bl, bs, g.s.ptr(), g.t.ptr(), g.r0.ptr(), x.ptr(), g.r.ptr(), pt, c3));
+                        CK(launch_bl_fin_r(bs, pt, nb3, c3));
+                        ge->if_k = 5;
+                    });
+                    CK(launch_bl_p(bl, bs, g.p.ptr(), g.v.ptr(), g.r.ptr(), h_iter, c2));
+                    ge->it_k = launches + 5;
+                    launches = outer;
+                });
+                residual64(dag, phi, x, c1);
+                CK(launch_bl_cycle(bs, nrm_rr.as<double>(), h_cycle, c1));
+                CK(launch_copy_f64(g.r.v.as<double>(), r64.v.as<double>(), nel, sm_count, c1));
+                ge->cyc_k = launches + 6;
+            });
+        } catch (...) {
+            launches = saved;
+            abandon_capture(cap_top);
+            throw;
+        }
+        launches = saved;
+        CK(cudaStreamEndCapture(cap_top, &ge->graph));
+        CK(cudaGraphInstantiate(&ge->exec, ge->graph, 0));
+        it = blk->graphs.emplace(key, std::move(ge)).first;
+    }
+    GraphEntry& ge = *it->second;
+    CK(cudaGraphLaunch(ge.exec, s));
+    BlState h;
+    CK(cudaMemcpyAsync(&h, bs, sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    launches += ge.pro_k + ge.cyc_k * h.cycles + ge.it_k * h.body_runs + ge.if_k * h.if_runs;
+    Result res;
+    res.sweeps.assign(n, h.cycles);
+    res.inner.assign(n, h.iters);
+    res.resid.assign(n, 0.0);
+    res.converged = true;
+    for (int i = 0; i < n; ++i) {
+        res.resid[i] = h.bb[i] > 0 ? sqrt(h.rr[i] / h.bb[i]) : 0.0;
+        if (!(h.rr[i] <= tol * tol * h.bb[i]) && h.bb[i] > 0.0) res.converged = false;
+    }
+    return res;
+}
+
+// out = M in captured on s: |in|^2, the outer states of the FP32 inner
+// solves (k_gl_prep: adaptive targets), out = 0, the inner start, the WHILE
+// node over the inner iterations (body on child), out += |in| e
+void Workspace::capture_precondition(bool dag, const FieldBuf& in, FieldBuf& out, int maxiter, cudaStream_t s,
+                                     cudaStream_t child) {
+    const int ci = 1;
+    const KrylovOps& o = ops_for(ci);
+    Inner& w = inner[ci];
+    SolverCtx k0 = ctx(false);
+    CK(launch_norm2(cfg[0].lc, in.ptr(), &k0, nrm_rr.as<double>(), s));
+    CK(launch_gl_prep(blk->state.as<GlState>(), ost.as<OState>(), nrm_rr.as<double>(), s));
+    CK(launch_copy_f64(out.v.as<double>(), nullptr, 24LL * S, sm_count, s));
+    const cudaGraphConditionalHandle h_in = new_handle(s);
+    SolverCtx k = ctx(true);
+    k.cond = h_in;
+    k.use_cond = 1;
+    CK(o.init(cfg[ci].lc, in.ptr(), w.x.ptr(), w.r.ptr(), w.r0.ptr(), w.p.ptr(), w.ph.ptr(), &k, maxiter, s));
+    cond_body(s, h_in, cudaGraphCondTypeWhile, child, [&](cudaStream_t c) { enqueue_iteration(ci, dag, k, c, false); });
+    CK(o.dc_update(cfg[ci].lc, out.ptr(), w.x.ptr(), &k, s));
+}
+
+// Gl-BiCGStab with its FP32 preconditioner as one graph (the iteration of
+// gl_bicgstab, Sec. 3.2 case D1):
+//   prologue: |phi|^2, X = 0, R = phi, state start (opens the cycle loop)
+//   WHILE cycle: R0 = R, P = R, rho = <R0, R>_F and the stop test
+//     WHILE iteration: PH = M P; V = A PH with <R0, V>; alpha = rho / <R0, V>_F;
+//       S = R - alpha V with X += alpha PH and |S|^2; the half-step test
+//       IF not converged: SH = M S; T = A SH; <T, S>, |T|^2; omega;
+//         X += omega SH, R = S - omega T with |R|^2, <R0, R>; the stop test, beta
+//       P = R + beta (P - omega V), and the iteration loop's condition
+//     FP64 true residual, another cycle while a rhs is above tol, R = r
+Workspace::Result Workspace::gl_bicgstab_graph(bool dag, const FieldBuf& phi, FieldBuf& x, double tol, int maxiter) {
+    ensure_cfg(0);
+    ensure_cfg(1);
+    ensure_cfg(3);
+    ensure_inner(1);
+    ensure_gl();
+    ensure_blk();
+    const int n = nrhs, max_cycles = 4, max_outer = 100;
+    const double delta = 1e-5;   // inner relative residual of a preconditioner call (the FP32 floor)
+    cudaStream_t s = stream;
+    GlState* gs = blk->state.as<GlState>();
+    double* pt = blk->partials.as<double>();
+    const LaunchCfg& bl = cfg[3].lc;
+    const int nb0 = cfg[0].lc.nblocks, nb3 = bl.nblocks;
+    const long long nel = 24LL * S;
+    const Blk::Key key{1, dag ? 1 : 0, phi.v.p, x.v.p, tol, maxiter};
+    auto it = blk->graphs.find(key);
+    if (it == blk->graphs.end()) {
+        const KrylovOps& o64 = ops_f64();
+        const FieldPtr none{nullptr, nullptr};
+        Gl& g = *gl;
+        auto ge = std::make_unique<GraphEntry>();
+        const long long saved = launches;
+        CK(cudaStreamBeginCapture(cap_top, cudaStreamCaptureModeThreadLocal));
+        try {
+            const cudaGraphConditionalHandle h_cycle = new_handle(cap_top);
+            launches = 0;
+            SolverCtx k0 = ctx(false);
+            CK(launch_norm2(cfg[0].lc, phi.ptr(), &k0, nrm_bb.as<double>(), cap_top));
+            CK(launch_copy_f64(x.v.as<double>(), nullptr, nel, sm_count, cap_top));
+            CK(launch_copy_f64(g.r.v.as<double>(), phi.v.as<double>(), nel, sm_count, cap_top));
+            CK(launch_gl_init(gs, n, nrm_bb.as<double>(), tol, delta, max_outer, max_cycles, ost.as<OState>(),
+                              h_cycle, cap_top));
+            ge->pro_k = 5;
+            ge->call_k = 7;   // norm2 (2), prep, out = 0, inner start (2), update
+            cond_body(cap_top, h_cycle, cudaGraphCondTypeWhile, cap_sweep, [&](cudaStream_t c1) {
+                launches = 0;
+                CK(launch_copy_f64(g.r0.v.as<double>(), g.r.v.as<double>(), nel, sm_count, c1));
+                CK(launch_copy_f64(g.p.v.as<double>(), g.r.v.as<double>(), nel, sm_count, c1));
+                CK(launch_gl_ts(bl, gs, g.r0.ptr(), g.r.ptr(), pt, c1));
+                const cudaGraphConditionalHandle h_iter = new_handle(c1);
+                CK(launch_gl_fin_start(gs, pt, nb3, h_iter, c1));
+                cond_body(c1, h_iter, cudaGraphCondTypeWhile, cap_stream, [&](cudaStream_t c2) {
+                    capture_precondition(dag, g.p, g.ph, maxiter, c2, blk->cs[0]);
+                    SolverCtx kp = ctx(false);
+                    kp.partials = pt;
+                    CK(o64.hop(cfg[0].lc, 1, dag, g.ph.ptr(), t64o.ptr(), 1.0, 0, nullptr, c2));
+                    CK(o64.tail(cfg[0].lc, 0, dag, RED_R0V, t64o.ptr(), g.ph.ptr(), none, g.v.ptr(), g.r0.ptr(), 1.0,
+                                -1.0, 2, &kp, nullptr, c2));
+                    CK(launch_gl_fin_alpha(gs, pt, nb0, c2));
+                    CK(launch_gl_s(bl, gs, g.r.ptr(), g.v.ptr(), g.ph.ptr(), g.s.ptr(), x.ptr(), pt, c2));
+                    const cudaGraphConditionalHandle h_if = new_handle(c2);
+                    CK(launch_gl_fin_s(gs, pt, nb3, h_if, c2));
+                    cond_body(c2, h_if, cudaGraphCondTypeIf, blk->cs[1], [&](cudaStream_t c3) {
+                        capture_precondition(dag, g.s, g.sh, maxiter, c3, blk->cs[0]);
+                        CK(o64.hop(cfg[0].lc, 1, dag, g.sh.ptr(), t64o.ptr(), 1.0, 0, nullptr, c3));
+                        CK(o64.tail(cfg[0].lc, 0, dag, RED_NONE, t64o.ptr(), g.sh.ptr(), none, g.t.ptr(), none, 1.0,
+                                    -1.0, 2, nullptr, nullptr, c3));
+                        CK(launch_gl_ts(bl, gs, g.t.ptr(), g.s.ptr(), pt, c3));
+                        CK(launch_gl_fin_omega(gs, pt, nb3, c3));
+                        CK(launch_gl_r(bl, gs, g.s.ptr(), g.t.ptr(), g.sh.ptr(), g.r0.ptr(), x.ptr(), g.r.ptr(), pt,
+                                       c3));
+                        CK(launch_gl_fin_r(gs, pt, nb3, c3));
+                    });
+                    CK(launch_gl_p(bl, gs, g.p.ptr(), g.v.ptr(), g.r.ptr(), h_iter, c2));
+                });
+                residual64(dag, phi, x, c1);
+                CK(launch_gl_cycle(gs, nrm_rr.as<double>(), h_cycle, c1));
+                CK(launch_copy_f64(g.r.v.as<double>(), r64.v.as<double>(), nel, sm_count, c1));
+            });
+            ge->cyc_k = 3 + 6;   // residual (3), copies (3), Frobenius start (2), cycle check
+            ge->it_k = 6;        // hop, tail, alpha, S update, half-step test, P update (the call counted apart)
+            ge->if_k = 6;        // hop, tail, <T, S>, omega, R update, stop test
+        } catch (...) {
+            launches = saved;
+            abandon_capture(cap_top);
+            throw;
+        }
+        launches = saved;
+        CK(cudaStreamEndCapture(cap_top, &ge->graph));
+        CK(cudaGraphInstantiate(&ge->exec, ge->graph, 0));
+        it = blk->graphs.emplace(key, std::move(ge)).first;
+    }
+    GraphEntry& ge = *it->second;
+    // the inner solves' WHILE cap and iteration total
+    pin[2] = maxiter + 8;
+    pin[5] = 0;
+    CK(cudaMemcpyAsync(loop_count.as<int>() + 1, pin + 2, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(loop_count.as<int>() + 3, pin + 5, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaGraphLaunch(ge.exec, s));
+    GlState h;
+    std::vector<OState> oo(n);
+    CK(cudaMemcpyAsync(&h, gs, sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(oo.data(), ost.p, n * sizeof(OState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pin + 5, loop_count.as<int>() + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    launches += ge.pro_k + ge.cyc_k * h.cycles + ge.it_k * h.body_runs + ge.if_k * h.if_runs +
+                ge.call_k * h.calls + (long long)ops_for(1).iteration_kernels(cfg[1].lc) * pin[5];
+    Result res;
+    res.sweeps.assign(n, h.calls);
+    res.inner.resize(n);
+    res.resid.assign(n, 0.0);
+    res.converged = true;
+    for (int i = 0; i < n; ++i) {
+        res.inner[i] = oo[i].inner_iters;
+        res.resid[i] = h.bb[i] > 0 ? sqrt(h.rr[i] / h.bb[i]) : 0.0;
+        if (!(h.rr[i] <= tol * tol * h.bb[i]) && h.bb[i] > 0.0) res.converged = false;
     }
     return res;
 }

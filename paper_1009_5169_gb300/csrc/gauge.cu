@@ -549,13 +549,15 @@ cudaError_t launch_gram64(const LaunchCfg& c, FieldPtr a, FieldPtr b, double* pa
     if (c.nrhs <= 8) {
         launch_pdl(k_gram64<8>, dim3(c.nblocks), dim3(dim3(c.TS, c.nrhs)), st, c.lats, c.nlat, c.nrhs, cf<P64>(a),
                    cf<P64>(b), partials);
-        launch_pdl(k_gram64_finish<8>, dim3(1), dim3(FIN_THREADS), st, c.lats, c.nrhs, c.nblocks,
-                   (const double*)partials, out);
+        if (out)
+            launch_pdl(k_gram64_finish<8>, dim3(1), dim3(FIN_THREADS), st, c.lats, c.nrhs, c.nblocks,
+                       (const double*)partials, out);
     } else {
         launch_pdl(k_gram64<16>, dim3(c.nblocks), dim3(dim3(c.TS, c.nrhs)), st, c.lats, c.nlat, c.nrhs, cf<P64>(a),
                    cf<P64>(b), partials);
-        launch_pdl(k_gram64_finish<16>, dim3(1), dim3(FIN_THREADS), st, c.lats, c.nrhs, c.nblocks,
-                   (const double*)partials, out);
+        if (out)
+            launch_pdl(k_gram64_finish<16>, dim3(1), dim3(FIN_THREADS), st, c.lats, c.nrhs, c.nblocks,
+                       (const double*)partials, out);
     }
     return cudaGetLastError();
 }

@@ -61,8 +61,9 @@ template <> struct AccOf<float> { using T = ff; };
 
 // Per-block partial sums: vals[j][q] of every thread (rhs = threadIdx.y * NR
 // + j) -> partials[(rhs * NQ + q) * gridDim.x + blockIdx.x], a fixed shuffle
-// tree per warp and a fixed sum over the warps of a rhs group.  Every thread
-// of the block calls it.  The lattice sums are formed by k_finish, launched
+// tree per warp and a fixed sum over the warps of a rhs group (the block's
+// threads write the rhs x NQ sums in turn, so NQ may exceed a warp).  Every
+// thread of the block calls it.  The lattice sums are formed by k_finish, launched
 // next on the same stream: the kernel boundary orders the partials, where a
 // last-block-done scheme inside the kernel pays device-scope fences on every
 // block's critical path.
@@ -84,9 +85,9 @@ __device__ __forceinline__ void block_partials(const A (&vals)[NR][NQ], int nrhs
             if (lane == 0) sw[w][j][q] = v;
         }
     __syncthreads();
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if (tid < (int)blockDim.y * NR * NQ) {
-        const int y = tid / (NR * NQ), jq = tid % (NR * NQ), j = jq / NQ, q = jq % NQ;
+    const int nt = blockDim.x * blockDim.y;
+    for (int e = threadIdx.y * blockDim.x + threadIdx.x; e < (int)blockDim.y * NR * NQ; e += nt) {
+        const int y = e / (NR * NQ), jq = e % (NR * NQ), j = jq / NQ, q = jq % NQ;
         const int rhs = y * NR + j;
         if (rhs < nrhs) {
             A s = acc_zero<A>();
@@ -187,6 +188,7 @@ __device__ __forceinline__ void fin_apply(const SolverCtx& ctx, int i, int tid, 
         reinterpret_cast<double2*>(out)[i] = make_double2(sres[2 * tid], sres[2 * tid + 1]);
         return;
     }
+    if (ctx.st == nullptr) return;
     KState& st = ctx.st[i];
     if (MODE == FIN_INIT || MODE == FIN_INIT_CG) {
         const OState& o = ctx.ost[i];
@@ -904,13 +906,15 @@ struct OpsImpl {
         using RV = typename PV::real;
         switch (red) {
             case RED_NONE: if (hz) SF_TAIL(RED_NONE, true); else SF_TAIL(RED_NONE, false); break;
+            // without solver states (the block solvers' own finishing kernels
+            // read the partials) only the tail runs
             case RED_R0V:
                 SF_TAIL(RED_R0V, false);
-                launch_finish<2, A, FIN_R0V, RV>(c, k, nullptr, 0, st);
+                if (k.st) launch_finish<2, A, FIN_R0V, RV>(c, k, nullptr, 0, st);
                 break;
             case RED_TS:
                 SF_TAIL(RED_TS, false);
-                launch_finish<3, A, FIN_TS, RV>(c, k, nullptr, 0, st);
+                if (k.st) launch_finish<3, A, FIN_TS, RV>(c, k, nullptr, 0, st);
                 break;
             case RED_NORM:
                 if (hz) SF_TAIL(RED_NORM, true); else SF_TAIL(RED_NORM, false);

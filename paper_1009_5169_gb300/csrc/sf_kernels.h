@@ -179,7 +179,7 @@ cudaError_t launch_multi_axpy64(const LaunchCfg&, int nvec, const double2* const
 cudaError_t launch_gamma5_64(long long total_elems, int Vpad, FieldPtr in, FieldPtr out, cudaStream_t);
 // Gram block G[i][j] = <a_i, b_j> of one lattice's block vectors -> out
 // (device, out[j * 2S + 2 i + (0, 1)], S = 8 for nrhs <= 8 else 16); partials
-// holds nrhs * 2S * nblocks doubles
+// holds nrhs * 2S * nblocks doubles; out NULL: the partials only
 cudaError_t launch_gram64(const LaunchCfg&, FieldPtr a, FieldPtr b, double* partials, double* out, cudaStream_t);
 // HMC trajectory (hmc.cu), canonical links and [(T+1) L^3][4][8] momenta:
 // gauge force (F and / or mom -= eps F), U <- exp(i dt P) U on the dynamic
