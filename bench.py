@@ -284,6 +284,11 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_us": round(t_cold * 1e6, 2),
                 "l2_warm_launch_us": round(t_warm * 1e6, 2), "peak_kind": peak_kind}
 
+    # ---------------- the FP64 kernels of the step against the FP64 pipe: the
+    # hop of the true residuals and the force (both bound by FP64 arithmetic on
+    # this GPU, whose FP64 rate is 1/64 of FP32's)
+    fp64 = fp64_roofline(sf, lat, lt, nrhs, stream, flush, dev)
+
     # ---------------- dslash on a lattice larger than L2 (HBM-bound case)
     hbm = None
     if not args.no_hbm_case and rank == 0:
@@ -419,7 +424,7 @@ def run_ours(args, rank, world, local_rank):
         "accuracy": {"max_true_rel_resid": resid, "sweeps_x": last["iters_outer"], "inner_iters_x": last["iters_inner"],
                      "sweeps_y": last["iters_outer_y"], "inner_iters_y": last["iters_inner_y"],
                      "solve_block_recheck": recheck},
-        "roofline": roofline, "dslash_hbm": hbm, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "roofline": roofline, "fp64_roofline": fp64, "dslash_hbm": hbm, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "comparators": comparators, "batched": batched, "hmc_trajectory": hmc, "learned": learned,
         "accuracy_configs": acc_cfg["summary"] if acc_cfg else None,
     }
@@ -643,6 +648,67 @@ def run_reference(args, rank, world):
                                       f"iterations per step) and the force"},
            "e2e": {"value": round(sps, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def _fp64_gemm_tflops(dev):
+    """Measured FP64 denominator: cuBLAS DGEMM (torch.matmul, 4096^3) timed
+    with CUDA events, TFLOP/s."""
+    import torch
+    n = 4096
+    g = torch.Generator(device=dev).manual_seed(7)
+    a = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        torch.matmul(a, b)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2.0 * n ** 3 * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+
+def fp64_roofline(sf, lat, lt, nrhs, stream, flush, dev):
+    """FLOP-based roofline of the FP64 hop (the true residuals' Dhat) and the
+    force kernel on the bench lattice, each launch timed alone with CUDA
+    events after an L2 flush.  Algorithmic FLOPs: the hop 1320 per site and
+    rhs (8 directions of projection, two SU(3) products and accumulation);
+    the force 336 per link and rhs (four spin projections, two 3 x 3 outer
+    products) + 470 per link (V M1 - M2 V^dag, the eight traces, the
+    scaling), on the (4T - 5) L^3 dynamic links that carry a fermion force."""
+    import torch
+    peak = _fp64_gemm_tflops(dev)
+    fshape = ((lt.T + 1) * lt.L ** 3, 4, 8)
+    F = torch.zeros(fshape, dtype=torch.float64, device=dev)
+
+    def timed(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        ev = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e-3
+
+    t_hop = timed(lambda: sf.wilson_hop_resident(lat, "fp64", nrhs, 1))
+    t_force = timed(lambda: sf.fermion_force_resident(lat, nrhs, F))
+    hop_flops = 1320.0 * lt.Vh * nrhs
+    links = (4 * lt.T - 5) * lt.L ** 3
+    force_flops = links * (336.0 * nrhs + 470.0)
+    out = {"unit": "TFLOP/s", "peak": round(peak, 3), "peak_kind": "measured cuBLAS DGEMM (4096^3) in this run",
+           "nominal_peak": 1.25}
+    for name, fl, t in (("k_hop<P64> (dslash H_oe)", hop_flops, t_hop), ("k_force", force_flops, t_force)):
+        ach = fl / t / 1e12
+        out[name] = {"bound": "alu", "achieved": round(ach, 3), "frac": round(ach / peak, 4),
+                     "frac_of_nominal": round(ach / 1.25, 4), "flops_per_launch": fl,
+                     "launch_us": round(t * 1e6, 2)}
+    return out
 
 
 def learned_section(args, dev, local_rank, stream):

@@ -274,6 +274,15 @@ sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double
  * one dslash kernel with events on that stream. */
 sf_status wilson_hop_resident(sf_lattice* lat, sf_prec prec, int nrhs, int out_parity);
 
+/* One launch of the FP64 force kernel of Eq. (3) on the lattice's resident
+ * full-lattice X and Y (those the last fermion_force or md_force_step with
+ * this nrhs packed; zero after creation), writing F (device memory of the
+ * lattice's device, layout [(T+1) L^3][4][8], only the entries of dynamic
+ * links; not cleared first).  Enqueued on the lattice's stream and not
+ * synchronised, so a caller can time exactly one force kernel with events
+ * on that stream.  SF_EINVAL if F is NULL, host memory or on another device. */
+sf_status fermion_force_resident(sf_lattice* lat, int nrhs, double* F);
+
 /* ---- learned preconditioner: a 4-layer 3^4-stencil convolutional network
  * on the full fermion lattice (widths 32 -> H -> H -> H -> 24, ReLU between
  * layers, H = 16 or 32), BF16 tensor-core kernels with FP32 accumulation.

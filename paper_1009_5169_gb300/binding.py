@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         L.wilson_hop_resident.argtypes = [vp, i, i, i]
         L.solve_block.argtypes = [vp, i, i, vp, vp, vp, d, i, ctypes.POINTER(SolveInfo)]
         L.fermion_force.argtypes = [vp, i, vp, vp, vp, vp, d]
+        L.fermion_force_resident.argtypes = [vp, i, vp]
         L.md_force_step.argtypes = [vp, i, i, vp, vp, vp, vp, vp, d, d, i, ctypes.POINTER(SolveInfo)]
         L.plaquette_action.argtypes = [vp, ctypes.POINTER(d)]
         L.gauge_force.argtypes = [vp, vp, vp, d]
@@ -120,7 +121,8 @@ def lib() -> ctypes.CDLL:
         L.sf_batch_destroy.argtypes = [vp]
         L.sf_batch_destroy.restype = None
         for fn in ("sf_lattice_create", "sf_lattice_set_links", "sf_lattice_set_tuning", "sf_lattice_get_tuning",
-                   "wilson_apply_block", "wilson_hop_resident", "solve_block", "fermion_force", "md_force_step",
+                   "wilson_apply_block", "wilson_hop_resident", "solve_block", "fermion_force", "fermion_force_resident",
+                   "md_force_step",
                    "plaquette_action", "sf_batch_create",
                    "sf_batch_solve"):
             getattr(L, fn).restype = ctypes.c_int
@@ -269,6 +271,13 @@ def fermion_force(lat: Lattice, X, Y, F=None, mom=None, eps: float = 0.0) -> Non
     if mom is not None:
         _check_size(mom, fb, "mom")
     _check(lib().fermion_force(lat.handle, nrhs, _ptr(X), _ptr(Y), _ptr(F), _ptr(mom), eps))
+
+
+def fermion_force_resident(lat: Lattice, nrhs: int, F) -> None:
+    """One force-kernel launch on the resident X, Y of the last force call
+    (profiling aid); F a device tensor of the force layout, not cleared."""
+    _check_size(F, (lat.T + 1) * lat.L ** 3 * 4 * 8 * 8, "F")
+    _check(lib().fermion_force_resident(lat.handle, nrhs, _ptr(F)))
 
 
 def md_force_step(lat: Lattice, algo: str, phi, X, Y, F=None, mom=None, eps: float = 0.0, tol: float = 1e-10,

@@ -2487,6 +2487,24 @@ void force_from_workspace(sf_lattice* lat, Workspace& w, double* F, double* mom,
 
 }  // namespace
 
+sf_status fermion_force_resident(sf_lattice* lat, int nrhs, double* F) {
+    return guarded([&] {
+        REQUIRE(lat != nullptr && F != nullptr, "NULL argument");
+        check_nrhs(nrhs);
+        cudaPointerAttributes a;
+        const bool known = cudaPointerGetAttributes(&a, F) == cudaSuccess;
+        if (!known) cudaGetLastError();
+        REQUIRE(known && a.type == cudaMemoryTypeDevice && a.device == lat->device,
+                "F must be device memory of the lattice's device");
+        CK(cudaSetDevice(lat->device));
+        Workspace& w = lattice_ws(lat, nrhs);
+        w.ensure_cfg(0);
+        ensure_odd(w);
+        CK(launch_force(w.cfg[0].per_lat[0], w.x64.ptr(), w.xo64.ptr(), w.y64.ptr(), w.yo64.ptr(), F, nullptr, 0.0,
+                        lat->stream));
+    });
+}
+
 sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double* Y, double* F, double* mom,
                         double eps) {
     return guarded([&] {

@@ -484,3 +484,23 @@ def test_staged_link_tiling_solves(sf, algo, L, T):
     ry = oracle.true_residual(U, Xn, Yn, L, T, 0.5, 0.13, dagger=True)
     assert np.all(rx <= 1.05e-10) and np.all(ry <= 1.05e-10), (rx, ry, info)
     lat.close()
+
+
+def test_force_resident_matches_fermion_force(sf):
+    """One resident force-kernel launch (the timing entry point) gives the
+    F of the last fermion_force call bitwise (same kernel, same resident
+    fields), and refuses a host F."""
+    L, T = 6, 7
+    U, lat = _lattice(sf, L, T, 0.3, 0.13, 0.5, seed=151)
+    X = torch.from_numpy(inputs.sources(L, T, 5, 152)).cuda()
+    Y = torch.from_numpy(inputs.sources(L, T, 5, 153)).cuda()
+    fshape = ((T + 1) * L ** 3, 4, 8)
+    F1 = torch.zeros(fshape, dtype=torch.float64, device="cuda")
+    sf.fermion_force(lat, X, Y, F1)
+    F2 = torch.zeros_like(F1)
+    sf.fermion_force_resident(lat, 5, F2)
+    torch.cuda.synchronize()
+    assert torch.equal(F1, F2)
+    with pytest.raises(sf.SFError):
+        sf.fermion_force_resident(lat, 5, torch.zeros(fshape, dtype=torch.float64))
+    lat.close()
