@@ -85,11 +85,18 @@ __device__ __forceinline__ void hop_dir(const LatDev& g, const SiteX& s, int cb,
         for (int j = 0; j < NR; ++j) {
             if (j < nval) {
                 cpx<R> p[4][3];
-                load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
                 cpx<R> h[2][3], w[2][3];
-                project<MU, SF>(p, h);
-                mul_link(U, h, w);
-                expand_add<MU, SF>(acc[j], w);
+                if constexpr (std::is_same<P, P16>::value) {
+                    const float sc = load_spinor_raw(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
+                    project<MU, SF>(p, h);
+                    mul_link(U, h, w);
+                    expand_fma<MU, SF>(acc[j], w, sc);
+                } else {
+                    load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
+                    project<MU, SF>(p, h);
+                    mul_link(U, h, w);
+                    expand_add<MU, SF>(acc[j], w);
+                }
             }
         }
     }
@@ -101,11 +108,18 @@ __device__ __forceinline__ void hop_dir(const LatDev& g, const SiteX& s, int cb,
         for (int j = 0; j < NR; ++j) {
             if (j < nval) {
                 cpx<R> p[4][3];
-                load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
                 cpx<R> h[2][3], w[2][3];
-                project<MU, SB>(p, h);
-                mul_link_dag(U, h, w);
-                expand_add<MU, SB>(acc[j], w);
+                if constexpr (std::is_same<P, P16>::value) {
+                    const float sc = load_spinor_raw(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
+                    project<MU, SB>(p, h);
+                    mul_link_dag(U, h, w);
+                    expand_fma<MU, SB>(acc[j], w, sc);
+                } else {
+                    load_spinor<P, R>(in, vbase<P>(g, r0 + j), g.Vpad, ncb, sbase(g, r0 + j), p);
+                    project<MU, SB>(p, h);
+                    mul_link_dag(U, h, w);
+                    expand_add<MU, SB>(acc[j], w);
+                }
             }
         }
     }
@@ -214,22 +228,22 @@ __device__ __forceinline__ void hop_apply(const LatDev& g, const HopBuf<P, NR>& 
                     p[(2 * k + 1) / 3][(2 * k + 1) % 3] = cpx<float>{b.s[j][k].z, b.s[j][k].w};
                 }
             } else {
-                const float sc = b.sc[j];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const float2 a = h2f(b.s[j][k].x), c = h2f(b.s[j][k].y), d = h2f(b.s[j][k].z),
                                  e = h2f(b.s[j][k].w);
-                    p[(4 * k) / 3][(4 * k) % 3] = cpx<float>{a.x * sc, a.y * sc};
-                    p[(4 * k + 1) / 3][(4 * k + 1) % 3] = cpx<float>{c.x * sc, c.y * sc};
-                    p[(4 * k + 2) / 3][(4 * k + 2) % 3] = cpx<float>{d.x * sc, d.y * sc};
-                    p[(4 * k + 3) / 3][(4 * k + 3) % 3] = cpx<float>{e.x * sc, e.y * sc};
+                    p[(4 * k) / 3][(4 * k) % 3] = cpx<float>{a.x, a.y};
+                    p[(4 * k + 1) / 3][(4 * k + 1) % 3] = cpx<float>{c.x, c.y};
+                    p[(4 * k + 2) / 3][(4 * k + 2) % 3] = cpx<float>{d.x, d.y};
+                    p[(4 * k + 3) / 3][(4 * k + 3) % 3] = cpx<float>{e.x, e.y};
                 }
             }
             cpx<float> h[2][3], w[2][3];
             project<MU, S>(p, h);
             if (FWD) mul_link(U, h, w);
             else mul_link_dag(U, h, w);
-            expand_add<MU, S>(acc[j], w);
+            if constexpr (std::is_same<P, P32>::value) expand_add<MU, S>(acc[j], w);
+            else expand_fma<MU, S>(acc[j], w, b.sc[j]);   // the FP16 scale, applied in the sum
         }
     }
 }
@@ -312,7 +326,9 @@ __device__ __forceinline__ void hop_dir_staged(const LatDev& g, const SiteX& s, 
     constexpr int S = FWD ? SF : -SF;
     const int ncb = neighbour_cb<MU, FWD ? +1 : -1>(g, s);
     cpx<float> p[4][3];
-    load_spinor<P, float>(in, vbase<P>(g, rhs), g.Vpad, ncb, sbase(g, rhs), p);
+    float sc = 1.f;
+    if constexpr (std::is_same<P, P16>::value) sc = load_spinor_raw(in, vbase<P>(g, rhs), g.Vpad, ncb, sbase(g, rhs), p);
+    else load_spinor<P, float>(in, vbase<P>(g, rhs), g.Vpad, ncb, sbase(g, rhs), p);
     cpx<float> h[2][3], w[2][3];
     project<MU, S>(p, h);
     constexpr int TS = HOP_SM_TS;
@@ -325,7 +341,8 @@ __device__ __forceinline__ void hop_dir_staged(const LatDev& g, const SiteX& s, 
     }
     if (FWD) mul_link(U, h, w);
     else mul_link_dag(U, h, w);
-    expand_add<MU, S>(acc, w);
+    if constexpr (std::is_same<P, P16>::value) expand_fma<MU, S>(acc, w, sc);   // the FP16 scale, in the sum
+    else expand_add<MU, S>(acc, w);
 }
 
 template <typename P, bool DAG>

@@ -198,6 +198,36 @@ __device__ __forceinline__ void expand_add(cpx<R> (&acc)[4][3], const cpx<R> (&u
     }
 }
 
+// acc += sc (the spin expansion of u): expand_add with the FP16 spinor scale
+// applied in the sum, one FFMA per real component in place of the add (the
+// loaded components are then used unscaled)
+__device__ __forceinline__ void acc_fma(cpx<float>& a, const cpx<float>& u, float s) {
+    a.re = fmaf(s, u.re, a.re);
+    a.im = fmaf(s, u.im, a.im);
+}
+template <int MU, int S>
+__device__ __forceinline__ void expand_fma(cpx<float> (&acc)[4][3], const cpx<float> (&u)[2][3], float sc) {
+    const float nsc = -sc;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc_fma(acc[0][a], u[0][a], sc);
+        acc_fma(acc[1][a], u[1][a], sc);
+        if (MU == 0) {
+            acc_fma(acc[2][a], u[0][a], S < 0 ? nsc : sc);
+            acc_fma(acc[3][a], u[1][a], S < 0 ? nsc : sc);
+        } else if (MU == 1) {
+            acc_fma(acc[2][a], S < 0 ? ti(u[1][a]) : tmi(u[1][a]), sc);
+            acc_fma(acc[3][a], S < 0 ? ti(u[0][a]) : tmi(u[0][a]), sc);
+        } else if (MU == 2) {
+            acc_fma(acc[2][a], u[1][a], S < 0 ? nsc : sc);
+            acc_fma(acc[3][a], u[0][a], S < 0 ? sc : nsc);
+        } else {
+            acc_fma(acc[2][a], S < 0 ? ti(u[0][a]) : tmi(u[0][a]), sc);
+            acc_fma(acc[3][a], S < 0 ? tmi(u[1][a]) : ti(u[1][a]), sc);
+        }
+    }
+}
+
 // ------------------------------------------------------ field access
 // Precision tags: storage type of a spinor field and its arithmetic type.
 struct P64 { using real = double; static constexpr int NC = 12; using vec = double2; };
@@ -264,6 +294,22 @@ __device__ __forceinline__ void load_spinor<P16, float>(const CField<P16>& f, lo
         p[(4 * k + 2) / 3][(4 * k + 2) % 3] = cpx<float>{c.x * sc, c.y * sc};
         p[(4 * k + 3) / 3][(4 * k + 3) % 3] = cpx<float>{d.x * sc, d.y * sc};
     }
+}
+
+// the FP16 spinor of (site, rhs) without its scale, which is returned (a
+// hop applies it once, in expand_fma)
+__device__ __forceinline__ float load_spinor_raw(const CField<P16>& f, long long base, int Vpad, int site,
+                                                 long long sbase, cpx<float> (&p)[4][3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint4 v = __ldg(f.v + base + (long long)k * Vpad + site);
+        float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+        p[(4 * k) / 3][(4 * k) % 3] = cpx<float>{a.x, a.y};
+        p[(4 * k + 1) / 3][(4 * k + 1) % 3] = cpx<float>{b.x, b.y};
+        p[(4 * k + 2) / 3][(4 * k + 2) % 3] = cpx<float>{c.x, c.y};
+        p[(4 * k + 3) / 3][(4 * k + 3) % 3] = cpx<float>{d.x, d.y};
+    }
+    return __ldg(f.scale + sbase + site);
 }
 
 template <typename P, typename R>
