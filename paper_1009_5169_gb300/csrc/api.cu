@@ -1019,6 +1019,11 @@ void Workspace::autotune(int ci) {
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (env_flag("SF_TUNE_LOG")) {   // every candidate's best time, for diagnosing a choice
+        fprintf(stderr, "sf autotune: %d lattice(s), %d rhs, precision %d:", nlat, nrhs, ci);
+        for (const Cand& cd : cands) fprintf(stderr, " [TS %d NR %d mode %d %.1f us]", cd.TS, cd.NR, cd.pipe, cd.ms * 125.0f);
+        fprintf(stderr, " -> TS %d NR %d mode %d\n", bTS, bNR, bpipe);
+    }
     set_tiling(ci, bTS, bNR, bpipe);
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune_cache[key] = {bTS, bNR, bpipe};
