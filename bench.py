@@ -919,7 +919,7 @@ def main():
                     help="fix the inner solve's tiling of the timed step instead of autotuning it")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-train-fields", type=int, default=40)
-    ap.add_argument("--learned-epochs", type=int, default=15)
+    ap.add_argument("--learned-epochs", type=int, default=50)
     ap.add_argument("--learned-heldout", type=int, default=10)
     ap.add_argument("--learned-slow-fields", type=int, default=2,
                     help="held-out fields the slow comparators (FP64 BiCGStab, FGCR without the network) run on")
