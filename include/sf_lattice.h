@@ -117,13 +117,20 @@ typedef enum {
      * of the single systems (relative residual 1e-5 each, all rhs in one
      * launch); restarted from the recomputed FP64 residual while a rhs is
      * above tol.  iters_outer reports the preconditioner calls, iters_inner
-     * the FP32 iterations.  One lattice only (not batches). */
+     * the FP32 iterations.  One lattice only (not batches).  If it ends above
+     * tol (a breakdown that restarting does not cure, e.g. linearly dependent
+     * right-hand sides), FP32-inner BiCGStab under FP64 defect correction
+     * continues each rhs from its iterate and adds its counts. */
     SF_SOLVE_GL_BICGSTAB = 6,
     /* Bl-BiCGStab in FP64 (the paper's case C, Sec. 3.2): the rhs share one
      * Krylov space through nrhs x nrhs coefficient matrices; restarted from
      * the recomputed FP64 residual while a rhs is above tol.  iters_inner
      * reports the block iterations (each applies Dhat to every rhs twice),
-     * iters_outer the restarts + 1.  One lattice only (not batches). */
+     * iters_outer the restarts + 1.  One lattice only (not batches).  The
+     * nrhs x nrhs systems are solved by Householder QR; a rank-deficient block
+     * (linearly dependent right-hand sides) breaks down, and FP32-inner
+     * BiCGStab under FP64 defect correction continues each rhs from its
+     * iterate, adding its counts. */
     SF_SOLVE_BL_BICGSTAB = 7,
     /* the learned preconditioner in mixed precision: FP64 defect correction
      * (r = phi - Dhat x recomputed in FP64, x += |r| e) around flexible GCR in

@@ -1817,6 +1817,23 @@ Workspace::Result Workspace::bl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf
 }
 
 // ---------------------------------------------------------------- device-resident block solvers
+
+// A block solve that ends above tol (a breakdown that restarting does not
+// cure, e.g. linearly dependent right-hand sides, or the cycle cap) is
+// continued from its iterate by FP32-inner BiCGStab under FP64 defect
+// correction, column by column; its sweeps and iterations are added.
+static void continue_per_rhs(Workspace& w, Workspace::Result& res, bool dag, const FieldBuf& phi, FieldBuf& x,
+                             double tol, int maxiter) {
+    if (res.converged) return;
+    Workspace::Result fb = w.solve(1, dag, phi, x, tol, maxiter, /*from_x=*/true);
+    for (size_t i = 0; i < res.sweeps.size(); ++i) {
+        res.sweeps[i] += fb.sweeps[i];
+        res.inner[i] += fb.inner[i];
+        res.resid[i] = fb.resid[i];
+    }
+    res.converged = fb.converged;
+}
+
 void Workspace::ensure_blk() {
     if (!blk) {
         blk.reset(new Blk());
@@ -1934,6 +1951,7 @@ Workspace::Result Workspace::bl_bicgstab_graph(bool dag, const FieldBuf& phi, Fi
         res.resid[i] = h.bb[i] > 0 ? sqrt(h.rr[i] / h.bb[i]) : 0.0;
         if (!(h.rr[i] <= tol * tol * h.bb[i]) && h.bb[i] > 0.0) res.converged = false;
     }
+    continue_per_rhs(*this, res, dag, phi, x, tol, maxiter);
     return res;
 }
 
@@ -2076,6 +2094,7 @@ Workspace::Result Workspace::gl_bicgstab_graph(bool dag, const FieldBuf& phi, Fi
         res.resid[i] = h.bb[i] > 0 ? sqrt(h.rr[i] / h.bb[i]) : 0.0;
         if (!(h.rr[i] <= tol * tol * h.bb[i]) && h.bb[i] > 0.0) res.converged = false;
     }
+    continue_per_rhs(*this, res, dag, phi, x, tol, maxiter);
     return res;
 }
 

@@ -504,3 +504,24 @@ def test_force_resident_matches_fermion_force(sf):
     with pytest.raises(sf.SFError):
         sf.fermion_force_resident(lat, 5, torch.zeros(fshape, dtype=torch.float64))
     lat.close()
+
+
+@pytest.mark.parametrize("algo", ["bl_bicgstab", "gl_bicgstab"])
+def test_block_solvers_linearly_dependent_sources(sf, algo):
+    """A block with two equal right-hand sides (the degenerate case of the
+    block method: R0^H V is singular) still returns X and Y to 1e-10 by the
+    oracle's residual, status OK: Bl-BiCGStab's QR reports the breakdown and
+    the per-rhs continuation finishes the solve."""
+    L, T, kappa, theta = 6, 7, 0.12, 0.5
+    U, lat = _lattice(sf, L, T, 0.3, kappa, theta, seed=161)
+    phi = inputs.sources(L, T, 4, 162)
+    phi[2] = phi[0]
+    pd = torch.from_numpy(phi).cuda()
+    X, Y = torch.empty_like(pd), torch.empty_like(pd)
+    info = sf.solve_block(lat, algo, pd, X, Y, tol=1e-10, maxiter=3000)
+    assert info["status"] == "SF_OK", info
+    Xn, Yn = X.cpu().numpy(), Y.cpu().numpy()
+    rx = oracle.true_residual(U, phi, Xn, L, T, theta, kappa)
+    ry = oracle.true_residual(U, Xn, Yn, L, T, theta, kappa, dagger=True)
+    assert np.all(rx <= 1.05e-10) and np.all(ry <= 1.05e-10), (rx, ry, info)
+    lat.close()
