@@ -409,9 +409,9 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_hmc and rank == 0:
         hmc = hmc_section(args, sf, inputs, lt, U_d, nrhs, tol, fshape, dev, local_rank)
 
-    learned = None
+    learned, learned_check = None, None
     if not args.no_learned and rank == 0:
-        learned = learned_section(args, dev, local_rank, stream)
+        learned_check, learned = learned_section(args, dev, local_rank, stream)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -430,7 +430,7 @@ def run_ours(args, rank, world, local_rank):
     }
     lat.close()
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, host_solution, acc_cfg)
+        out["cpu_baseline"] = cpu_baseline(args, host_solution, acc_cfg, learned_check)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -469,14 +469,16 @@ def _per_rhs_relerr(a, b):
     return (np.linalg.norm((a - b).reshape(n, -1), axis=1) / np.linalg.norm(b.reshape(n, -1), axis=1)).tolist()
 
 
-def cpu_baseline(args, host_solution=None, acc_cfg=None):
+def cpu_baseline(args, host_solution=None, acc_cfg=None, learned_check=None):
     """The FP64 oracle as it stands, timed on the host cores: full steps of
     the bench workload (every field's X and Y to the workload's residual and
     the force), once with OpenMP on every core this process may run on and
     once single-threaded.  The same leg checks the GPU's results with the
     oracle: its true residuals of the bench step's X and Y, and on the 16^4
     kappa 0.134 workload every RHS's error of the FP32- and FP16-inner
-    solutions against the oracle's own solutions (solved to 1e-12)."""
+    solutions against the oracle's own solutions (solved to 1e-12), and the
+    oracle's residuals of every solver's X and Y on the first held-out 24^4
+    field of the learned-preconditioner comparison."""
     import oracle
     from paper_1009_5169_gb300 import inputs
     w = inputs.workload(args.workload)
@@ -509,7 +511,57 @@ def cpu_baseline(args, host_solution=None, acc_cfg=None):
             "err_x_vs_oracle_1e-10": _per_rhs_relerr(X, Xo), "err_y_vs_oracle_1e-10": _per_rhs_relerr(Y, Yo)}
     if acc_cfg is not None:
         out["oracle_check_sf16"] = _oracle_check_sf16(acc_cfg, cores)
+    if learned_check is not None and learned_check.get("solutions"):
+        lc = learned_check["lattice"]
+        chk = {"workload": f"held-out field 0 of the learned comparison ({lc.L}^3x{lc.T}, kappa {lc.kappa}, "
+                           f"eps {lc.eps}): the oracle's true residuals |Phi - Dhat X|/|Phi| and |X - Dhat^dag Y|/|X| "
+                           f"per RHS of each solver's X, Y"}
+        for algo, (X, Y) in learned_check["solutions"].items():
+            rx = oracle.true_residual(learned_check["U"], learned_check["phi"], X, lc.L, lc.T, lc.theta, lc.kappa)
+            ry = oracle.true_residual(learned_check["U"], X, Y, lc.L, lc.T, lc.theta, lc.kappa, dagger=True)
+            chk[algo] = {"oracle_resid_x": [float(v) for v in rx], "oracle_resid_y": [float(v) for v in ry]}
+        out["oracle_check_learned"] = chk
+    out["configs"] = _oracle_configs(cores, acc_cfg, learned_check)
     return out
+
+
+def _oracle_configs(cores, acc_cfg, learned_check):
+    """The oracle's time on the other workloads: the 8^4 FP64 1-RHS step in
+    full; the 16^4 solves from the oracle check above; the 24^4 field from a
+    measured cost per BiCGStab iteration times iteration counts (a full
+    oracle solve there takes minutes)."""
+    import oracle
+    from paper_1009_5169_gb300 import inputs
+    res = {}
+    w = inputs.workload("sf8_plain_1rhs")
+    lt = w.lattices[0]
+    U = lt.make_links()
+    phi = lt.make_sources(w.nrhs)
+    t, _, _, info = _oracle_full_step(w, U, phi)
+    res[w.name] = {"seconds_per_step": round(t, 3), "cores": cores, "kind": "measured",
+                   "sample": f"X and Y by FP64 BiCGStab to {w.tol} ({int(info['iters_x'][0])}+"
+                             f"{int(info['iters_y'][0])} iterations) and the force"}
+    if acc_cfg is not None:
+        res["sf16_mixed"] = {"kind": "measured", "sample": "X and Y of the 5 RHS to 1e-12 (no force): "
+                                                          "cpu_baseline.oracle_check_sf16.oracle.seconds"}
+    if learned_check is not None and "U" in learned_check:
+        lc = learned_check["lattice"]
+        n_it = 10
+        t0 = time.perf_counter()
+        oracle.bicgstab(learned_check["U"], learned_check["phi"][:1], lc.L, lc.T, lc.theta, lc.kappa, tol=1e-30,
+                        maxiter=n_it)
+        per_it = (time.perf_counter() - t0) / n_it
+        e = {"seconds_per_bicgstab_iteration": round(per_it, 4), "cores": cores, "kind": "extrapolated",
+             "sample": f"{n_it} oracle BiCGStab iterations on one RHS of a {lc.L}^3x{lc.T} field, timed"}
+        its = learned_check.get("iters", {}).get("bicgstab")
+        if its is not None:
+            ix, iy = its
+            total = int(sum(ix)) + 5 * int(iy)
+            e["seconds_per_solve_pair"] = round(per_it * total, 1)
+            e["sample"] += (f"; times {total} iterations: the library's FP64 BiCGStab on the same field, X per RHS "
+                            f"{ix} and 5 x the largest Y count {iy} (no force)")
+        res["sf24_cnn"] = e
+    return res
 
 
 def _oracle_check_sf16(acc_cfg, cores):
@@ -722,7 +774,9 @@ def learned_section(args, dev, local_rank, stream):
     precision form (FP32 flexible GCR under FP64 defect correction) is timed
     against the same solver without the network, plain FP64 BiCGStab on the
     5-RHS block, and the FP32-inner mixed solves; every answer is judged by
-    the library's FP64 true residual."""
+    the library's FP64 true residual.  Returns (the first held-out field's
+    links, sources and every solver's X, Y for the oracle check of the
+    cpu_baseline leg; the section's summary)."""
     import torch
     from paper_1009_5169_gb300 import binding as sf
     from paper_1009_5169_gb300 import inputs
@@ -774,12 +828,19 @@ def learned_section(args, dev, local_rank, stream):
     rows = 2 * w.nrhs * big.V
     res = {}
     slow = ("bicgstab", "fgcr_mixed")
+    # the first held-out field's solutions go to the oracle check of the cpu_baseline leg
+    check = {"solutions": {}}
     for h in range(args.learned_heldout):
         lt = inputs.Lattice(big.L, big.T, big.eps, big.kappa, inputs.SEED_BASE + 1000 + h)
-        lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(lt.make_links()).to(dev),
+        Uh = lt.make_links()
+        lat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(Uh).to(dev),
                          device=local_rank)
         sf.set_preconditioner(lat, net)
-        phi = torch.from_numpy(inputs.sources(lt.L, lt.T, w.nrhs, inputs.SEED_BASE + 1000 + h)).to(dev)
+        phin = inputs.sources(lt.L, lt.T, w.nrhs, inputs.SEED_BASE + 1000 + h)
+        phi = torch.from_numpy(phin).to(dev)
+        if h == 0:
+            check.update(lattice=lt, U=Uh, phi=phin)
+        del Uh
         X, Y = torch.empty_like(phi), torch.empty_like(phi)
         for algo in ("fgcr_cnn_mixed", "fgcr_mixed", "bicgstab", "mixed_dc", "cg_normal"):
             if algo in slow and h >= args.learned_slow_fields:
@@ -795,6 +856,9 @@ def learned_section(args, dev, local_rank, stream):
             e["iters_x"].append(info["iters_inner"])
             e["iters_y"].append(info["iters_inner_y"])
             e["max_true_rel_resid"] = max(e["max_true_rel_resid"], max(info["true_resid"]), max(info["true_resid_y"]))
+            if h == 0:
+                check["solutions"][algo] = (X.cpu().numpy(), Y.cpu().numpy())
+                check.setdefault("iters", {})[algo] = (list(info["iters_inner_rhs"][:w.nrhs]), info["iters_inner_y"])
         sf.set_preconditioner(lat, None)
         lat.close()
     net.close()
@@ -803,7 +867,7 @@ def learned_section(args, dev, local_rank, stream):
                    "mean_iters": [round(mean(v["iters_x"]), 1), round(mean(v["iters_y"]), 1)]}
                for k, v in res.items()}
     learned = summary["fgcr_cnn_mixed"]["mean_ms"]
-    return {"workload": f"{big.L}^3x{big.T} SF, kappa {big.kappa}, eps {big.eps}, {w.nrhs} RHS, tol {w.tol}; "
+    return check, {"workload": f"{big.L}^3x{big.T} SF, kappa {big.kappa}, eps {big.eps}, {w.nrhs} RHS, tol {w.tol}; "
                         f"{args.learned_heldout} held-out fields (plain FP64 BiCGStab and FGCR without the network "
                         f"on the first {args.learned_slow_fields})",
             "network": f"4 x 3^4 conv, widths {inputs.cnn_widths(hidden)}, BF16 operands, FP32 accumulation, "

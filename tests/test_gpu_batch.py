@@ -65,9 +65,12 @@ def test_batch_matches_single_lattice_solves(sf):
         lat.close()
 
 
-def test_batched_uneven_workload(sf):
+@pytest.mark.parametrize("algo", ["mixed_dc", "cg_normal"])
+def test_batched_uneven_workload(sf, algo):
     """The full batched workload: 24 fields, 8 each of 8^4, 12^4, 16^4, eps
-    cycling 0.15/0.25/0.35, kappa 0.13, 5 RHS, FP32 inner / FP64 outer."""
+    cycling 0.15/0.25/0.35, kappa 0.13, 5 RHS, FP32 inner / FP64 outer, by
+    the defect-correction BiCGStab and by the normal-equation CG route (the
+    one the bench times); X and Y of every RHS of all 24 lattices judged by
+    the oracle's true residual."""
     w = inputs.workload("batched_uneven")
-    # the oracle checks one lattice of each size; the library's FP64 residual all 24
-    _solve_batch(sf, w.lattices, w.nrhs, "mixed_dc", w.tol, check=[0, 9, 23])
+    _solve_batch(sf, w.lattices, w.nrhs, algo, w.tol, check=range(len(w.lattices)))

@@ -10,6 +10,8 @@
 * 24^4 SF, eps 0.2, kappa 0.134, 5 RHS (the learned-preconditioner
   workload): the normal-equation route's X and Y judged by the oracle's
   true residual.
+* 32^3 x 32, 5 RHS (the HBM-bound hop measurement): the FP32 and FP16 hops
+  in the measured launch configuration against the oracle's FP64 hop.
 
 The error of a solution against the oracle's is bounded by the condition
 number times the residual, so it is reported, not gated; the gate on it is
@@ -139,3 +141,35 @@ def test_sf24_cg_normal_against_oracle_residual(sf):
     assert np.all(rx <= w.tol * TOL_FACTOR), (rx, info)
     assert np.all(ry <= w.tol * TOL_FACTOR), (ry, info)
     lat.close()
+
+
+@pytest.fixture(scope="module")
+def hbm_case():
+    """The 32^3 x 32 field and even-site input of the HBM-bound hop
+    measurement, with the oracle's FP64 H_oe of that input."""
+    L, T, eps, theta, nrhs = 32, 32, 0.2, 0.5, 5
+    U = inputs.links(L, T, eps, inputs.SEED_BASE + 32)
+    x = inputs.sources(L, T, nrhs, 4242)
+    full = oracle.join_eo(x, np.zeros_like(x), L, T)
+    ref = oracle.split_eo(oracle.hop(U, full, L, T, theta), L, T)[1]
+    return L, T, theta, U, x, ref
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 4e-3)])
+def test_hbm_case_hop_against_oracle(sf, hbm_case, prec, tol):
+    """The hopping term H_oe (Eq. 2 with the SF boundaries of Sec. 4) at the
+    size and in the launch configuration of the bench's HBM-bound
+    measurement: 32^3 x 32, 5 RHS, 32-site tiles with the links staged in
+    shared memory (5120 blocks of 160 threads).  Every output site of every
+    RHS against the oracle's FP64 hop of the same even-site input, within the
+    storage precision of the operands."""
+    L, T, theta, U, x, ref = hbm_case
+    lat = sf.Lattice(L, T, theta, 0.13, 4.52, torch.from_numpy(U).cuda())
+    lat.set_tuning(prec, 32, 1, 2)
+    assert lat.get_tuning(prec, x.shape[0]) == (32, 1, 2)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    sf.wilson_apply_block(lat, "hop_oe", prec, xd, out)
+    got = out.cpu().numpy()
+    lat.close()
+    assert relerr(got, ref) <= tol
