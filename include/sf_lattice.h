@@ -371,10 +371,19 @@ sf_status plaquette_action_noalloc(int L, int T, double beta, const double* link
 /* Message of the last failure on this thread ("" if none). */
 const char* sf_last_error(void);
 
-/* ---- batches: several lattices (any sizes) solved by one launch per kernel.
- * The lattices must live on the same device and stay alive while the batch
- * exists; their links may change between solves. */
+/* ---- batches: several lattices (any sizes) solved by one launch per kernel
+ * and group of lattices (spec batching of many independent fields; the
+ * paper solves its five equations per field, Sec. 3.2).  At create the
+ * lattices are grouped so that each group's inner-loop working set (FP32
+ * links and six FP32 vectors per RHS) fits in three quarters of the L2 cache;
+ * a lattice larger than that forms a group of its own.  Groups are solved one
+ * after the other, each with its own autotuned tiling.  The lattices must
+ * live on the same device and stay alive while the batch exists; their links
+ * may change between solves. */
 sf_status sf_batch_create(sf_batch** out, int nlat, sf_lattice* const* lats, int nrhs);
+
+/* Number of lattice groups the batch is solved as (-1 for NULL). */
+int sf_batch_num_groups(const sf_batch* b);
 
 /* solve_block on every lattice of the batch; phi[l], X[l], Y[l] are lattice
  * l's arrays (Y may be NULL as a whole), info an array of nlat (or NULL). */

@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(SolveInfo)]
         L.sf_batch_destroy.argtypes = [vp]
         L.sf_batch_destroy.restype = None
+        L.sf_batch_num_groups.argtypes = [vp]
+        L.sf_batch_num_groups.restype = i
         for fn in ("sf_lattice_create", "sf_lattice_set_links", "sf_lattice_set_tuning", "sf_lattice_get_tuning",
                    "wilson_apply_block", "wilson_hop_resident", "solve_block", "fermion_force", "fermion_force_resident",
                    "md_force_step",
@@ -372,7 +374,8 @@ def hmc_trajectory(lat: Lattice, algo: str, eta, mom, uniform: float, nsteps: in
 
 
 class Batch:
-    """Several lattices (any sizes) solved with one launch per kernel."""
+    """Several lattices (any sizes) solved with one launch per kernel and
+    group of lattices whose working set fits in L2 (see sf_batch_create)."""
 
     def __init__(self, lattices: Sequence[Lattice], nrhs: int):
         self.lattices = list(lattices)
@@ -397,6 +400,10 @@ class Batch:
         for d in out:
             d["status"] = STATUS[rc]
         return out
+
+    @property
+    def num_groups(self) -> int:
+        return int(lib().sf_batch_num_groups(self._h))
 
     def close(self) -> None:
         if self._h:

@@ -2808,9 +2808,60 @@ sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double
 // ---------------------------------------------------------------- batches
 }  // extern "C"
 
+// A batch is solved as groups of its lattices, one launch per kernel and group.
+// The groups are formed so that each group's inner-loop working set (FP32 links
+// and the six FP32 vectors of every RHS) fits in three quarters of L2: a
+// group that spills L2 runs its stencils from HBM, where they go no faster than
+// the same lattices solved one after the other (measured: eight 16^4 lattices in
+// one launch, 27.9 us per lattice and Dhat against 28.9 us alone), while lattices
+// too small to fill the GPU gain from sharing launches (eight 8^4: 3.7x).  Each
+// group has its own workspace, so the autotuner picks the tiling per group.
 struct sf_batch {
-    Workspace ws;
+    std::vector<std::unique_ptr<Workspace>> groups;
+    std::vector<std::pair<int, int>> where;   // lattice -> (group, index in the group)
+    int nlat = 0, nrhs = 0, device = 0;
 };
+
+namespace {
+size_t solve_working_set(const sf_lattice* l, int nrhs) {
+    return (size_t)l->Vpad * (4 * 2 * 3 * 16 + (size_t)nrhs * 6 * 96);
+}
+
+// first-fit decreasing: the largest lattices first, each into the first group
+// with room; a lattice above the budget gets a group of its own
+std::vector<std::vector<int>> group_lattices(const std::vector<sf_lattice*>& v, int nrhs, size_t budget) {
+    std::vector<int> order(v.size());
+    for (size_t i = 0; i < v.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return solve_working_set(v[a], nrhs) > solve_working_set(v[b], nrhs);
+    });
+    std::vector<std::vector<int>> groups;
+    std::vector<size_t> used;
+    for (int l : order) {
+        const size_t ws = solve_working_set(v[l], nrhs);
+        size_t g = 0;
+        while (g < groups.size() && used[g] + ws > budget) ++g;
+        if (g == groups.size()) {
+            groups.emplace_back();
+            used.push_back(0);
+        }
+        groups[g].push_back(l);
+        used[g] += ws;
+    }
+    for (auto& g : groups) std::sort(g.begin(), g.end());   // lattices keep their order inside a group
+    return groups;
+}
+
+size_t batch_budget(int device) {
+    if (const char* e = getenv("SF_BATCH_BUDGET_BYTES")) {   // tests: force several groups
+        const long long v = atoll(e);
+        if (v > 0) return (size_t)v;
+    }
+    int l2 = 0;
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device));
+    return (size_t)l2 / 4 * 3;
+}
+}  // namespace
 
 extern "C" {
 
@@ -2827,7 +2878,19 @@ sf_status sf_batch_create(sf_batch** out, int nlat, sf_lattice* const* lats, int
         }
         CK(cudaSetDevice(v[0]->device));
         std::unique_ptr<sf_batch> b(new sf_batch());
-        b->ws.setup(v, nrhs);
+        b->nlat = nlat;
+        b->nrhs = nrhs;
+        b->device = v[0]->device;
+        b->where.resize(nlat);
+        for (const auto& g : group_lattices(v, nrhs, batch_budget(v[0]->device))) {
+            std::vector<sf_lattice*> gl;
+            for (int l : g) {
+                b->where[l] = {(int)b->groups.size(), (int)gl.size()};
+                gl.push_back(v[l]);
+            }
+            b->groups.emplace_back(new Workspace());
+            b->groups.back()->setup(gl, nrhs);
+        }
         *out = b.release();
     });
 }
@@ -2840,46 +2903,58 @@ sf_status sf_batch_solve(sf_batch* b, sf_algo algo, const double* const* phi, do
         REQUIRE(b != nullptr && phi != nullptr && X != nullptr, "NULL argument");
         REQUIRE(tol > 0 && tol < 1, "tol must be in (0, 1)");
         REQUIRE(maxiter >= 1, "maxiter must be >= 1");
-        Workspace& w = b->ws;
         const int ci = algo_index(algo);
         REQUIRE(ci < 3 || ci == 5, "batches run the BiCGStab and CG algorithms");
         const bool normal = (ci == 5);
-        CK(cudaSetDevice(w.device));
-        w.launches = 0;
-        w.ensure_cfg(0);
-        w.ensure_cfg(normal ? 1 : ci);
-        cudaStream_t s = w.stream;
-        for (int l = 0; l < w.nlat; ++l) {
-            REQUIRE(phi[l] != nullptr && X[l] != nullptr, "NULL array in batch");
-            const size_t bytes = (size_t)w.nrhs * w.lats[l]->Vh * 24 * sizeof(double);
-            const double* d = to_device(phi[l], bytes, w.io, s);
-            CK(ops_f64().pack(w.cfg[0].per_lat[l], d, w.phi64.ptr(), s));
-            if (d != phi[l]) CK(cudaStreamSynchronize(s));
-            w.launches += 1;
-        }
-        Workspace::Result rx, ry;
-        if (normal) {
-            w.solve_normal(w.phi64, tol, maxiter, rx, ry, /*check_y=*/true);
-        } else {
-            rx = w.solve(ci, false, w.phi64, w.x64, tol, maxiter);
-            if (Y) ry = w.solve(ci, true, w.x64, w.y64, tol, maxiter);
-        }
-        for (int l = 0; l < w.nlat; ++l) {
-            const size_t bytes = (size_t)w.nrhs * w.lats[l]->Vh * 24 * sizeof(double);
-            double* dX = out_device(X[l], bytes, w.io);
-            CK(ops_f64().unpack(w.cfg[0].per_lat[l], w.x64.ptr(), dX, s));
-            finish_out(X[l], dX, bytes, s);
-            if (Y && Y[l]) {
-                double* dY = out_device(Y[l], bytes, w.io);
-                CK(ops_f64().unpack(w.cfg[0].per_lat[l], w.y64.ptr(), dY, s));
-                finish_out(Y[l], dY, bytes, s);
+        for (int l = 0; l < b->nlat; ++l) REQUIRE(phi[l] != nullptr && X[l] != nullptr, "NULL array in batch");
+        CK(cudaSetDevice(b->device));
+        std::vector<Workspace::Result> rxs(b->groups.size()), rys(b->groups.size());
+        std::vector<long long> launches(b->groups.size(), 0);
+        for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+            Workspace& w = *b->groups[gi];
+            std::vector<int> members;   // batch indices of the group's lattices, in group order
+            for (int l = 0; l < b->nlat; ++l)
+                if (b->where[l].first == (int)gi) members.push_back(l);
+            w.launches = 0;
+            w.ensure_cfg(0);
+            w.ensure_cfg(normal ? 1 : ci);
+            cudaStream_t s = w.stream;
+            for (int k = 0; k < w.nlat; ++k) {
+                const int l = members[k];
+                const size_t bytes = (size_t)w.nrhs * w.lats[k]->Vh * 24 * sizeof(double);
+                const double* d = to_device(phi[l], bytes, w.io, s);
+                CK(ops_f64().pack(w.cfg[0].per_lat[k], d, w.phi64.ptr(), s));
+                if (d != phi[l]) CK(cudaStreamSynchronize(s));
+                w.launches += 1;
             }
+            if (normal) {
+                w.solve_normal(w.phi64, tol, maxiter, rxs[gi], rys[gi], /*check_y=*/true);
+            } else {
+                rxs[gi] = w.solve(ci, false, w.phi64, w.x64, tol, maxiter);
+                if (Y) rys[gi] = w.solve(ci, true, w.x64, w.y64, tol, maxiter);
+            }
+            for (int k = 0; k < w.nlat; ++k) {
+                const int l = members[k];
+                const size_t bytes = (size_t)w.nrhs * w.lats[k]->Vh * 24 * sizeof(double);
+                double* dX = out_device(X[l], bytes, w.io);
+                CK(ops_f64().unpack(w.cfg[0].per_lat[k], w.x64.ptr(), dX, s));
+                finish_out(X[l], dX, bytes, s);
+                if (Y && Y[l]) {
+                    double* dY = out_device(Y[l], bytes, w.io);
+                    CK(ops_f64().unpack(w.cfg[0].per_lat[k], w.y64.ptr(), dY, s));
+                    finish_out(Y[l], dY, bytes, s);
+                }
+            }
+            CK(cudaStreamSynchronize(s));
+            launches[gi] = w.launches;
+            if (!rxs[gi].converged || (Y && !rys[gi].converged)) noconv = true;
         }
-        CK(cudaStreamSynchronize(s));
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (info)
-            for (int l = 0; l < w.nlat; ++l) fill_info(info + l, rx, Y ? &ry : nullptr, l, w.nrhs, secs, w.launches);
-        if (!rx.converged || (Y && !ry.converged)) noconv = true;
+            for (int l = 0; l < b->nlat; ++l) {
+                const auto [gi, k] = b->where[l];
+                fill_info(info + l, rxs[gi], Y ? &rys[gi] : nullptr, k, b->nrhs, secs, launches[gi]);
+            }
     });
     if (st == SF_OK && noconv) {
         g_err = "solver stopped above tolerance";
@@ -2888,10 +2963,13 @@ sf_status sf_batch_solve(sf_batch* b, sf_algo algo, const double* const* phi, do
     return st;
 }
 
+int sf_batch_num_groups(const sf_batch* b) { return b ? (int)b->groups.size() : -1; }
+
 void sf_batch_destroy(sf_batch* b) {
     if (!b) return;
-    cudaSetDevice(b->ws.device);
-    if (b->ws.stream) cudaStreamSynchronize(b->ws.stream);
+    cudaSetDevice(b->device);
+    for (auto& w : b->groups)
+        if (w->stream) cudaStreamSynchronize(w->stream);
     delete b;
 }
 

@@ -18,12 +18,14 @@ def sf():
     return binding
 
 
-def _solve_batch(sf, lts, nrhs, algo, tol, check):
+def _solve_batch(sf, lts, nrhs, algo, tol, check, groups=None):
     Us = [lt.make_links() for lt in lts]
     phis = [lt.make_sources(nrhs) for lt in lts]
     lats = [sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, torch.from_numpy(U).cuda())
             for lt, U in zip(lts, Us)]
     b = sf.Batch(lats, nrhs)
+    if groups is not None:
+        assert b.num_groups == groups
     P = [torch.from_numpy(p).cuda() for p in phis]
     X = [torch.empty_like(p) for p in P]
     Y = [torch.empty_like(p) for p in P]
@@ -48,6 +50,25 @@ def test_small_uneven_batch(sf, algo):
     lts = [inputs.Lattice(4, 4, 0.3, 0.125, 101), inputs.Lattice(6, 5, 0.35, 0.13, 102),
            inputs.Lattice(8, 8, 0.25, 0.13, 103), inputs.Lattice(4, 7, 0.2, 0.12, 104)]
     _solve_batch(sf, lts, 3, algo, 1e-10, check=range(len(lts)))
+
+
+@pytest.mark.parametrize("algo", ["mixed_dc", "cg_normal"])
+def test_batch_split_into_groups(sf, algo, monkeypatch):
+    """A batch whose lattices do not fit the grouping budget together is
+    solved as several groups (first-fit, largest first), each with its own
+    workspace and tiling; every lattice still meets the oracle's residual.
+    The budget here admits the 8^4 lattice alone and the three smaller ones
+    together."""
+    lts = [inputs.Lattice(4, 4, 0.3, 0.125, 101), inputs.Lattice(6, 5, 0.35, 0.13, 102),
+           inputs.Lattice(8, 8, 0.25, 0.13, 103), inputs.Lattice(4, 7, 0.2, 0.12, 104)]
+    nrhs = 3
+    ws = [lt.L ** 3 * (lt.T - 1) // 2 for lt in lts]
+    vpad = [(v + 63) // 64 * 64 for v in ws]
+    per = [v * (4 * 2 * 3 * 16 + nrhs * 6 * 96) for v in vpad]
+    budget = max(per[0] + per[1] + per[3], per[2])
+    assert per[2] + min(per[0], per[1], per[3]) > budget
+    monkeypatch.setenv("SF_BATCH_BUDGET_BYTES", str(budget))
+    _solve_batch(sf, lts, nrhs, algo, 1e-10, check=range(len(lts)), groups=2)
 
 
 def test_batch_matches_single_lattice_solves(sf):
