@@ -399,6 +399,7 @@ def run_ours(args, rank, world, local_rank):
                                "X and Y to 1e-10, FP32 inner / FP64 outer", "algo": balgo,
                    "batched_solves_per_s": round(len(blats) / tb, 2), "batch_ms": round(tb * 1e3, 2),
                    "one_lattice_at_a_time_ms": round(ts * 1e3, 2), "speedup": round(ts / tb, 2),
+                   "groups": batch.num_groups,
                    "max_true_rel_resid": max(max(max(i["true_resid"]), max(i["true_resid_y"])) for i in binfo)}
         batch.close()
         for bl in blats:
