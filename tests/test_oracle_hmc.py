@@ -1,10 +1,14 @@
 """Pins of the HMC trajectory oracle (gauge force, link exponential,
-leapfrog) against what the mathematics fixes: central finite differences of
-the plaquette action (with scipy's expm, not the oracle's exponential),
-closed forms of the exponential, the O(dt^2) energy error of leapfrog and its
-time reversibility.  A wrong sign, a dropped staple or a wrong boundary rule
-in the gauge force breaks the finite differences; a wrong kick order or
-sign breaks the dt^2 scaling and reversibility."""
+leapfrog, the Omelyan integrator) against what the mathematics fixes: central
+finite differences of the plaquette action (with scipy's expm, not the
+oracle's exponential), closed forms of the exponential, the O(dt^2) energy
+error of both integrators and their time reversibility, the Omelyan
+integrator at lam = 1/2 reducing to the leapfrog, and its smaller energy
+error at the minimum-norm lam for the same number of force evaluations.  A
+wrong sign, a dropped staple or a wrong boundary rule in the gauge force
+breaks the finite differences; a wrong kick order or sign breaks the dt^2
+scaling and reversibility; a misplaced lam breaks the lam = 1/2 reduction or
+the comparison with the leapfrog."""
 import numpy as np
 import pytest
 import scipy.linalg
@@ -126,3 +130,49 @@ def test_leapfrog_is_reversible(mdcase):
     m = hmc.dynamic_mask(c["L"], c["T"])
     assert np.max(np.abs(U2 - c["U"])) < 1e-10
     assert np.max(np.abs(-P2[m] - c["P"][m])) < 1e-9
+
+
+def _om(c, nsteps, dt, U=None, P=None, lam=hmc.OMELYAN_LAMBDA):
+    return hmc.omelyan(c["U"] if U is None else U, c["P"] if P is None else P, c["phi"], c["L"], c["T"],
+                       c["theta"], c["kappa"], c["beta"], nsteps, dt, lam=lam)
+
+
+def test_omelyan_with_half_is_leapfrog(mdcase):
+    """lam = 1/2: the middle kick vanishes and the two half drifts make one, so
+    the trajectory is the leapfrog's of the same step (to rounding)."""
+    c = mdcase
+    Ua, Pa, a0, a1 = _om(c, 3, 0.05, lam=0.5)
+    Ub, Pb, b0, b1 = _traj(c, 3, 0.05)
+    m = hmc.dynamic_mask(c["L"], c["T"])
+    assert np.max(np.abs(Ua - Ub)) < 1e-13
+    assert np.max(np.abs(Pa[m] - Pb[m])) < 1e-12
+    assert abs((sum(a1) - sum(a0)) - (sum(b1) - sum(b0))) < 1e-10
+
+
+def test_omelyan_energy_error_is_second_order(mdcase):
+    c = mdcase
+    _, _, h0, h1 = _om(c, 4, 0.05)
+    _, _, g0, g1 = _om(c, 8, 0.025)
+    dh1 = sum(h1) - sum(h0)
+    dh2 = sum(g1) - sum(g0)
+    assert abs(dh1) > 1e-6
+    assert 3.2 < dh1 / dh2 < 4.8, (dh1, dh2)
+
+
+def test_omelyan_is_reversible(mdcase):
+    c = mdcase
+    U1, P1, _, _ = _om(c, 3, 0.05)
+    U2, P2, _, _ = _om(c, 3, 0.05, U=U1, P=-P1)
+    m = hmc.dynamic_mask(c["L"], c["T"])
+    assert np.max(np.abs(U2 - c["U"])) < 1e-10
+    assert np.max(np.abs(-P2[m] - c["P"][m])) < 1e-9
+
+
+def test_omelyan_beats_leapfrog_at_equal_force_count(mdcase):
+    """The minimum-norm parameter makes the leading error small: with the
+    same number of force evaluations (Omelyan, 4 steps of dt: 9; leapfrog, 8
+    steps of dt / 2: 9) the energy error is several times smaller."""
+    c = mdcase
+    _, _, h0, h1 = _om(c, 4, 0.05)
+    _, _, g0, g1 = _traj(c, 8, 0.025)
+    assert abs(sum(h1) - sum(h0)) < 0.5 * abs(sum(g1) - sum(g0))
