@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -623,7 +624,8 @@ def hmc_section(args, sf, inputs, lt, U_d, nrhs, tol, fshape, dev, local_rank):
     equilibrium by MD trajectories accepted unconditionally (untimed), then
     trajectories with fresh momenta and pseudo-fermions and the Metropolis
     test are timed; reports dH, the acceptance and the time per trajectory
-    and per accepted trajectory."""
+    and per accepted trajectory, for the leapfrog and then for the Omelyan
+    integrator over the same trajectory length at the same force count."""
     import torch
     hlat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, U_d, device=local_rank)
     nst, dt = args.hmc_steps, args.hmc_dt
@@ -655,7 +657,29 @@ def hmc_section(args, sf, inputs, lt, U_d, nrhs, tol, fshape, dev, local_rank):
         acc.append(bool(d["accepted"]))
         iters += d["inner_iters"]
         launches += d["kernel_launches"]
+    # the same trajectory length with the Omelyan integrator at half the
+    # steps (two force evaluations per step: the same force count, +1)
+    nst_o = max(1, nst // 2)
+    dt_o = dt * nst / nst_o
+    dho, acco, mso = [], [], []
+    for k in range(args.hmc_traj):
+        P, eta, u = draws(2000 + k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d = sf.hmc_trajectory(hlat, args.algo, eta, P, u, nst_o, dt_o, tol=tol, maxiter=args.maxiter,
+                              integrator="omelyan")
+        torch.cuda.synchronize()
+        mso.append(round((time.perf_counter() - t0) * 1e3, 2))
+        dho.append(round(d["dH"], 5))
+        acco.append(bool(d["accepted"]))
     hlat.close()
+    n_acco = sum(acco)
+    omelyan = {"integrator": f"Omelyan, Mryglod and Folk second-order minimum-norm, lambda {sf.OMELYAN_LAMBDA}",
+               "steps": nst_o, "dt": dt_o, "force_evals_per_trajectory": 2 * nst_o + 1, "dH": dho, "accepted": acco,
+               "acceptance": round(n_acco / max(1, len(acco)), 3),
+               "mean_min_1_exp_minus_dH": round(statistics.mean(min(1.0, math.exp(-x)) for x in dho), 3) if dho else None,
+               "ms_per_trajectory": round(statistics.mean(mso), 2) if mso else None,
+               "ms_per_accepted_trajectory": round(sum(mso) / n_acco, 2) if n_acco else None}
     n_acc = sum(acc)
     V4 = lt.L ** 3 * lt.T * 6
     return {"workload": f"{lt.L}^3x{lt.T} SF, beta {lt.beta}, {nrhs} pseudo-fermions phi = Dhat eta, Gaussian "
@@ -664,9 +688,11 @@ def hmc_section(args, sf, inputs, lt, U_d, nrhs, tol, fshape, dev, local_rank):
                                "dH": dh_therm,
                                "plaquette_action_per_plaquette": [round(p / (lt.beta * V4), 5) for p in plaq[::max(1, len(plaq) // 8)]]},
             "trajectories": args.hmc_traj, "dH": dhs, "accepted": acc, "acceptance": round(n_acc / max(1, len(acc)), 3),
+            "mean_min_1_exp_minus_dH": round(statistics.mean(min(1.0, math.exp(-x)) for x in dhs), 3) if dhs else None,
             "ms": ms, "ms_per_trajectory": round(statistics.mean(ms), 2) if ms else None,
             "ms_per_accepted_trajectory": round(sum(ms) / n_acc, 2) if n_acc else None,
-            "force_evals_per_trajectory": nst + 1, "inner_iters": iters, "kernel_launches": launches}
+            "force_evals_per_trajectory": nst + 1, "inner_iters": iters, "kernel_launches": launches,
+            "omelyan": omelyan}
 
 
 def run_reference(args, rank, world):

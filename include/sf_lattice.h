@@ -255,7 +255,7 @@ typedef struct {
     double s_gauge[2];      /* plaquette action */
     double s_fermion[2];    /* sum_i |Dhat^{-1} phi_i|^2 */
     double dH;              /* H(end) - H(start) */
-    int force_evals;        /* fermion force evaluations (nsteps + 1) */
+    int force_evals;        /* fermion force evaluations (leapfrog nsteps + 1, Omelyan 2 nsteps + 1) */
     int inner_iters;        /* inner solver iterations summed over them (X and Y) */
     double seconds;
     long long kernel_launches;
@@ -272,6 +272,18 @@ typedef struct {
  * with sf_lattice_set_links. */
 sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom, int nsteps,
                            double dt, double tol, int maxiter, sf_md_info* info);
+
+/* The same trajectory with the second-order minimum-norm integrator of
+ * Omelyan, Mryglod and Folk (2003), two force evaluations per step: per step
+ * P -= lambda dt F; U <- exp(i dt/2 P) U; P -= (1 - 2 lambda) dt F;
+ * U <- exp(i dt/2 P) U; P -= lambda dt F (the last kick of a step and the
+ * first of the next merged).  lambda = 0.1931833275037836 minimises the norm
+ * of the leading error terms; lambda must lie in (0, 1/2) (SF_EINVAL), and
+ * lambda -> 1/2 gives the leapfrog.  The paper names the HMC algorithm
+ * (Sec. 2) without its integrator. */
+sf_status sf_md_trajectory_omelyan(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom,
+                                   int nsteps, double dt, double lambda, double tol, int maxiter,
+                                   sf_md_info* info);
 
 /* One launch of the hopping-term kernel H_oe (out_parity 1) or H_eo
  * (out_parity 0) for nrhs fields in precision prec, on the lattice's

@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.sf_lattice_update_links.argtypes = [vp, vp, d]
         L.sf_lattice_get_links.argtypes = [vp, vp]
         L.sf_md_trajectory.argtypes = [vp, i, i, vp, vp, i, d, d, i, ctypes.POINTER(MdInfo)]
+        L.sf_md_trajectory_omelyan.argtypes = [vp, i, i, vp, vp, i, d, d, d, i, ctypes.POINTER(MdInfo)]
         L.plaquette_action_noalloc.argtypes = [i, i, d, vp, vp, i, vp]
         L.plaquette_action_noalloc.restype = ctypes.c_int
         L.sf_cnn_num_params.argtypes = [i]
@@ -337,16 +338,27 @@ def get_links(lat: Lattice, out) -> None:
     _check(lib().sf_lattice_get_links(lat.handle, _ptr(out)))
 
 
+OMELYAN_LAMBDA = 0.1931833275037836
+
+
 def md_trajectory(lat: Lattice, algo: str, phi, mom, nsteps: int, dt: float, tol: float = 1e-10,
-                  maxiter: int = 10000, allow_noconv: bool = False) -> dict:
-    """One leapfrog MD trajectory (gauge + fermion force for the pseudo-fermions
-    phi); moves the lattice's links and mom in place; returns the Hamiltonian
-    parts at both ends and dH."""
+                  maxiter: int = 10000, allow_noconv: bool = False, integrator: str = "leapfrog",
+                  lam: float = OMELYAN_LAMBDA) -> dict:
+    """One MD trajectory (gauge + fermion force for the pseudo-fermions phi)
+    by the leapfrog or the Omelyan integrator (parameter lam); moves the
+    lattice's links and mom in place; returns the Hamiltonian parts at both
+    ends and dH."""
     nrhs = _nrhs_of(phi, lat.Vh * 24 * 8)
     _check_size(mom, _mom_bytes(lat), "mom")
     info = MdInfo()
-    rc = lib().sf_md_trajectory(lat.handle, ALGOS[algo], nrhs, _ptr(phi), _ptr(mom), nsteps, dt, tol, maxiter,
-                                ctypes.byref(info))
+    if integrator == "leapfrog":
+        rc = lib().sf_md_trajectory(lat.handle, ALGOS[algo], nrhs, _ptr(phi), _ptr(mom), nsteps, dt, tol, maxiter,
+                                    ctypes.byref(info))
+    elif integrator == "omelyan":
+        rc = lib().sf_md_trajectory_omelyan(lat.handle, ALGOS[algo], nrhs, _ptr(phi), _ptr(mom), nsteps, dt, lam,
+                                            tol, maxiter, ctypes.byref(info))
+    else:
+        raise ValueError(f"integrator must be leapfrog or omelyan, got {integrator!r}")
     _check(rc, allow_noconv)
     d = info.as_dict()
     d["status"] = STATUS[rc]
@@ -354,7 +366,7 @@ def md_trajectory(lat: Lattice, algo: str, phi, mom, nsteps: int, dt: float, tol
 
 
 def hmc_trajectory(lat: Lattice, algo: str, eta, mom, uniform: float, nsteps: int, dt: float,
-                   tol: float = 1e-10, maxiter: int = 10000) -> dict:
+                   tol: float = 1e-10, maxiter: int = 10000, integrator: str = "leapfrog") -> dict:
     """One HMC trajectory with the caller's random numbers: pseudo-fermions
     phi = Dhat eta from the Gaussian even-site fields eta (so S_f = |eta|^2 at
     the start), an MD trajectory from the momenta mom, and the Metropolis
@@ -366,7 +378,7 @@ def hmc_trajectory(lat: Lattice, algo: str, eta, mom, uniform: float, nsteps: in
     wilson_apply_block(lat, "dhat", "fp64", eta, phi)
     old = torch.empty((lat.T + 1) * lat.L ** 3 * 4 * 18, dtype=torch.float64, device=eta.device)
     get_links(lat, old)
-    d = md_trajectory(lat, algo, phi, mom, nsteps, dt, tol, maxiter)
+    d = md_trajectory(lat, algo, phi, mom, nsteps, dt, tol, maxiter, integrator=integrator)
     d["accepted"] = bool(uniform < math.exp(min(0.0, -d["dH"])))
     if not d["accepted"]:
         lat.set_links(old)

@@ -2722,8 +2722,13 @@ sf_status sf_lattice_get_links(sf_lattice* lat, double* links) {
     });
 }
 
-sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom, int nsteps,
-                           double dt, double tol, int maxiter, sf_md_info* info) {
+}  // extern "C"
+
+namespace {
+// One MD trajectory; lam < 0: the leapfrog, else the second-order
+// minimum-norm integrator of Omelyan, Mryglod and Folk with parameter lam.
+sf_status md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom, int nsteps,
+                        double dt, double lam, double tol, int maxiter, sf_md_info* info) {
     bool noconv = false;
     sf_status st = guarded([&] {
         const auto t0 = std::chrono::steady_clock::now();
@@ -2776,13 +2781,29 @@ sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double
         memset(&out, 0, sizeof out);
         out.kinetic[0] = sumsq(lat, nmom, dM, 0.5);
         gauge_action(&out.s_gauge[0]);
-        out.s_fermion[0] = kick(0.5 * dt);
-        double sf_end = out.s_fermion[0];
-        for (int k = 0; k < nsteps; ++k) {
-            CK(launch_link_update(lat->L, lat->T, lat->canon.as<double>(), dM, dt, s));
+        // U <- exp(i e P) U and the prepared copies
+        auto drift = [&](double e) {
+            CK(launch_link_update(lat->L, lat->T, lat->canon.as<double>(), dM, e, s));
             prepare_links(lat);
             launches += 2;
-            sf_end = kick(k == nsteps - 1 ? 0.5 * dt : dt);
+        };
+        double sf_end;
+        if (lam < 0.0) {   // leapfrog
+            out.s_fermion[0] = kick(0.5 * dt);
+            sf_end = out.s_fermion[0];
+            for (int k = 0; k < nsteps; ++k) {
+                drift(dt);
+                sf_end = kick(k == nsteps - 1 ? 0.5 * dt : dt);
+            }
+        } else {           // kick lam dt, drift dt/2, kick (1 - 2 lam) dt, drift dt/2, kick lam dt
+            out.s_fermion[0] = kick(lam * dt);
+            sf_end = out.s_fermion[0];
+            for (int k = 0; k < nsteps; ++k) {
+                drift(0.5 * dt);
+                kick((1.0 - 2.0 * lam) * dt);
+                drift(0.5 * dt);
+                sf_end = kick(k == nsteps - 1 ? lam * dt : 2.0 * lam * dt);
+            }
         }
         out.kinetic[1] = sumsq(lat, nmom, dM, 0.5);
         gauge_action(&out.s_gauge[1]);
@@ -2803,6 +2824,23 @@ sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double
         return SF_ENOCONV;
     }
     return st;
+}
+}  // namespace
+
+extern "C" {
+
+sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom, int nsteps,
+                           double dt, double tol, int maxiter, sf_md_info* info) {
+    return md_trajectory(lat, algo, nrhs, phi, mom, nsteps, dt, -1.0, tol, maxiter, info);
+}
+
+sf_status sf_md_trajectory_omelyan(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom,
+                                   int nsteps, double dt, double lambda, double tol, int maxiter, sf_md_info* info) {
+    if (!(lambda > 0.0 && lambda < 0.5)) {
+        g_err = "lambda must be in (0, 1/2)";
+        return SF_EINVAL;
+    }
+    return md_trajectory(lat, algo, nrhs, phi, mom, nsteps, dt, lambda, tol, maxiter, info);
 }
 
 // ---------------------------------------------------------------- batches

@@ -1,5 +1,6 @@
 """GPU parity of the HMC trajectory pieces (gauge force, link update, the
-leapfrog trajectory around Alg. 2) against the FP64 oracle, through the C ABI.
+leapfrog and Omelyan trajectories around Alg. 2) against the FP64 oracle,
+through the C ABI.
 
 Tolerances: the gauge force and the link exponential are single FP64
 evaluations (1e-12 / 1e-13 relative); the trajectory composes solves to
@@ -99,6 +100,40 @@ def test_md_trajectory_matches_oracle_leapfrog(sf, mdcase, algo):
         assert abs(info["kinetic"][0] - h0[0]) <= 1e-12 * h0[0]
         assert abs([info["kinetic"], info["s_gauge"], info["s_fermion"]][k][1] - h1[k]) <= 1e-9 * abs(h1[k])
     assert abs(info["dH"] - (sum(h1) - sum(h0))) <= 1e-7
+    lat.close()
+
+
+@pytest.mark.parametrize("algo", ["mixed_dc", "cg_normal"])
+def test_md_trajectory_matches_oracle_omelyan(sf, mdcase, algo):
+    """The Omelyan (second-order minimum-norm) trajectory against the oracle's
+    on the same inputs: two force evaluations per step."""
+    c = mdcase
+    L, T = c["L"], c["T"]
+    Uo, Po, h0, h1 = hmc.omelyan(c["U"], c["P"], c["phi"], L, T, c["theta"], c["kappa"], c["beta"], 3, 0.05)
+    lat = _lat(sf, c["U"], L, T, c["theta"], c["kappa"], c["beta"])
+    mom = torch.from_numpy(c["P"].copy()).cuda()
+    info = sf.md_trajectory(lat, algo, torch.from_numpy(c["phi"]).cuda(), mom, 3, 0.05, tol=1e-12,
+                            integrator="omelyan")
+    assert info["force_evals"] == 7
+    out = torch.empty(((T + 1) * L ** 3, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    sf.get_links(lat, out)
+    assert relerr(out.cpu().numpy(), Uo) <= 1e-9
+    assert relerr(mom.cpu().numpy(), Po) <= 1e-8
+    for k in range(3):
+        assert abs([info["kinetic"], info["s_gauge"], info["s_fermion"]][k][1] - h1[k]) <= 1e-9 * abs(h1[k])
+    assert abs(info["dH"] - (sum(h1) - sum(h0))) <= 1e-7
+    lat.close()
+
+
+def test_omelyan_rejects_bad_lambda(sf, mdcase):
+    c = mdcase
+    lat = _lat(sf, c["U"], c["L"], c["T"], c["theta"], c["kappa"], c["beta"])
+    mom = torch.from_numpy(c["P"].copy()).cuda()
+    for lam in (0.0, 0.5, -0.1, 0.7):
+        with pytest.raises(sf.SFError):
+            sf.md_trajectory(lat, "cg_normal", torch.from_numpy(c["phi"]).cuda(), mom, 1, 0.05,
+                             integrator="omelyan", lam=lam)
+    assert np.array_equal(mom.cpu().numpy(), c["P"])
     lat.close()
 
 
