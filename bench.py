@@ -624,8 +624,9 @@ def hmc_section(args, sf, inputs, lt, U_d, nrhs, tol, fshape, dev, local_rank):
     equilibrium by MD trajectories accepted unconditionally (untimed), then
     trajectories with fresh momenta and pseudo-fermions and the Metropolis
     test are timed; reports dH, the acceptance and the time per trajectory
-    and per accepted trajectory, for the leapfrog and then for the Omelyan
-    integrator over the same trajectory length at the same force count."""
+    and per accepted trajectory, for the leapfrog, the Omelyan integrator over
+    the same trajectory length at the same force count, and the leapfrog with
+    the gauge force on 4 substeps per step."""
     import torch
     hlat = sf.Lattice(lt.L, lt.T, lt.theta, lt.kappa, lt.beta, U_d, device=local_rank)
     nst, dt = args.hmc_steps, args.hmc_dt
@@ -672,7 +673,26 @@ def hmc_section(args, sf, inputs, lt, U_d, nrhs, tol, fshape, dev, local_rank):
         mso.append(round((time.perf_counter() - t0) * 1e3, 2))
         dho.append(round(d["dH"], 5))
         acco.append(bool(d["accepted"]))
+    # the leapfrog again with the gauge force on 4 substeps of each step
+    # (two time scales: the same fermion force count)
+    dhm, accm, msm = [], [], []
+    for k in range(args.hmc_traj):
+        P, eta, u = draws(3000 + k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d = sf.hmc_trajectory(hlat, args.algo, eta, P, u, nst, dt, tol=tol, maxiter=args.maxiter, gauge_substeps=4)
+        torch.cuda.synchronize()
+        msm.append(round((time.perf_counter() - t0) * 1e3, 2))
+        dhm.append(round(d["dH"], 5))
+        accm.append(bool(d["accepted"]))
     hlat.close()
+    n_accm = sum(accm)
+    two_scales = {"integrator": "leapfrog, gauge force on 4 substeps per step (Sexton-Weingarten)", "steps": nst,
+                  "dt": dt, "force_evals_per_trajectory": nst + 1, "dH": dhm, "accepted": accm,
+                  "acceptance": round(n_accm / max(1, len(accm)), 3),
+                  "mean_min_1_exp_minus_dH": round(statistics.mean(min(1.0, math.exp(-x)) for x in dhm), 3) if dhm else None,
+                  "ms_per_trajectory": round(statistics.mean(msm), 2) if msm else None,
+                  "ms_per_accepted_trajectory": round(sum(msm) / n_accm, 2) if n_accm else None}
     n_acco = sum(acco)
     omelyan = {"integrator": f"Omelyan, Mryglod and Folk second-order minimum-norm, lambda {sf.OMELYAN_LAMBDA}",
                "steps": nst_o, "dt": dt_o, "force_evals_per_trajectory": 2 * nst_o + 1, "dH": dho, "accepted": acco,
@@ -692,7 +712,7 @@ def hmc_section(args, sf, inputs, lt, U_d, nrhs, tol, fshape, dev, local_rank):
             "ms": ms, "ms_per_trajectory": round(statistics.mean(ms), 2) if ms else None,
             "ms_per_accepted_trajectory": round(sum(ms) / n_acc, 2) if n_acc else None,
             "force_evals_per_trajectory": nst + 1, "inner_iters": iters, "kernel_launches": launches,
-            "omelyan": omelyan}
+            "omelyan": omelyan, "two_time_scales": two_scales}
 
 
 def run_reference(args, rank, world):

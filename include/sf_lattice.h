@@ -285,6 +285,19 @@ sf_status sf_md_trajectory_omelyan(sf_lattice* lat, sf_algo algo, int nrhs, cons
                                    int nsteps, double dt, double lambda, double tol, int maxiter,
                                    sf_md_info* info);
 
+/* The leapfrog trajectory on two time scales (Sexton and Weingarten 1992):
+ * the fermion force of Alg. 2 kicks with step dt, and each step's drift is
+ * split into gauge_substeps leapfrog steps of the (cheap) gauge force,
+ * h = dt / gauge_substeps:  P -= dt/2 F_f;  nsteps times { gauge_substeps
+ * times { P -= h/2 F_g; U <- exp(i h P) U; P -= h/2 F_g };  P -= dt/2 F_f },
+ * neighbouring half kicks merged.  gauge_substeps = 1 is sf_md_trajectory;
+ * it must lie in 1..1000 (SF_EINVAL).  force_evals counts the fermion force
+ * evaluations (nsteps + 1).  The paper names the HMC algorithm (Sec. 2)
+ * without its integrator. */
+sf_status sf_md_trajectory_two_scales(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom,
+                                      int nsteps, double dt, int gauge_substeps, double tol, int maxiter,
+                                      sf_md_info* info);
+
 /* One launch of the hopping-term kernel H_oe (out_parity 1) or H_eo
  * (out_parity 0) for nrhs fields in precision prec, on the lattice's
  * resident operand and result buffers (those wilson_apply_block last packed;

@@ -18,7 +18,12 @@ fixes none of these):
   (2003): per step P -= lam dt F; U <- exp(i dt/2 P) U; P -= (1 - 2 lam) dt F;
   U <- exp(i dt/2 P) U; P -= lam dt F, lam = 0.1931833275037836 (the value
   that minimises the norm of its leading error terms); the closing kick of a
-  step and the opening kick of the next add up to one kick of 2 lam dt.
+  step and the opening kick of the next add up to one kick of 2 lam dt;
+* two time scales (Sexton and Weingarten 1992): the fermion force kicks with
+  the leapfrog's step dt, and each step's drift is split into m gauge-force
+  leapfrog steps of dt / m:  P -= dt/2 F_f;  n times {m times {P -= dt/(2m) F_g;
+  U <- exp(i dt/m P) U; P -= dt/(2m) F_g};  P -= dt/2 F_f}, neighbouring
+  half kicks merged.
 """
 from __future__ import annotations
 
@@ -123,5 +128,29 @@ def omelyan(U, P, phi, L, T, theta, kappa, beta, nsteps, dt, lam=OMELYAN_LAMBDA,
         S1, Ff = fermion_action_and_force(U, phi, L, T, theta, kappa, tol)
         e = lam * dt if k == nsteps - 1 else 2.0 * lam * dt
         P -= e * (gauge_force(U, L, T, beta) + Ff)
+    K1, G1 = kinetic(P, L, T), plaquette_action(U, L, T, beta)
+    return U, P, (K0, G0, S0), (K1, G1, S1)
+
+
+def leapfrog_two_scales(U, P, phi, L, T, theta, kappa, beta, nsteps, dt, m, tol=1e-13):
+    """Nested leapfrog: the fermion force on steps of dt, the gauge force on
+    m substeps of dt / m per step (m = 1 is the leapfrog).  Returns (U, P, H
+    parts at start, at end)."""
+    mk = dynamic_mask(L, T)
+    P = P.copy()
+    P[~mk] = 0.0
+    K0, G0 = kinetic(P, L, T), plaquette_action(U, L, T, beta)
+    S0, Ff = fermion_action_and_force(U, phi, L, T, theta, kappa, tol)
+    h = dt / m
+    P -= 0.5 * h * gauge_force(U, L, T, beta)
+    P -= 0.5 * dt * Ff
+    S1 = S0
+    for k in range(nsteps):
+        for j in range(m):
+            U = update_links(U, P, h, L, T)
+            e = 0.5 * h if (k == nsteps - 1 and j == m - 1) else h
+            P -= e * gauge_force(U, L, T, beta)
+        S1, Ff = fermion_action_and_force(U, phi, L, T, theta, kappa, tol)
+        P -= (0.5 * dt if k == nsteps - 1 else dt) * Ff
     K1, G1 = kinetic(P, L, T), plaquette_action(U, L, T, beta)
     return U, P, (K0, G0, S0), (K1, G1, S1)

@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
         L.sf_lattice_get_links.argtypes = [vp, vp]
         L.sf_md_trajectory.argtypes = [vp, i, i, vp, vp, i, d, d, i, ctypes.POINTER(MdInfo)]
         L.sf_md_trajectory_omelyan.argtypes = [vp, i, i, vp, vp, i, d, d, d, i, ctypes.POINTER(MdInfo)]
+        L.sf_md_trajectory_two_scales.argtypes = [vp, i, i, vp, vp, i, d, i, d, i, ctypes.POINTER(MdInfo)]
         L.plaquette_action_noalloc.argtypes = [i, i, d, vp, vp, i, vp]
         L.plaquette_action_noalloc.restype = ctypes.c_int
         L.sf_cnn_num_params.argtypes = [i]
@@ -343,17 +344,21 @@ OMELYAN_LAMBDA = 0.1931833275037836
 
 def md_trajectory(lat: Lattice, algo: str, phi, mom, nsteps: int, dt: float, tol: float = 1e-10,
                   maxiter: int = 10000, allow_noconv: bool = False, integrator: str = "leapfrog",
-                  lam: float = OMELYAN_LAMBDA) -> dict:
+                  lam: float = OMELYAN_LAMBDA, gauge_substeps: int = 1) -> dict:
     """One MD trajectory (gauge + fermion force for the pseudo-fermions phi)
-    by the leapfrog or the Omelyan integrator (parameter lam); moves the
-    lattice's links and mom in place; returns the Hamiltonian parts at both
-    ends and dH."""
+    by the leapfrog (with the gauge force on gauge_substeps substeps of each
+    step: two time scales) or the Omelyan integrator (parameter lam); moves
+    the lattice's links and mom in place; returns the Hamiltonian parts at
+    both ends and dH."""
     nrhs = _nrhs_of(phi, lat.Vh * 24 * 8)
     _check_size(mom, _mom_bytes(lat), "mom")
     info = MdInfo()
-    if integrator == "leapfrog":
+    if integrator == "leapfrog" and gauge_substeps == 1:
         rc = lib().sf_md_trajectory(lat.handle, ALGOS[algo], nrhs, _ptr(phi), _ptr(mom), nsteps, dt, tol, maxiter,
                                     ctypes.byref(info))
+    elif integrator == "leapfrog":
+        rc = lib().sf_md_trajectory_two_scales(lat.handle, ALGOS[algo], nrhs, _ptr(phi), _ptr(mom), nsteps, dt,
+                                               gauge_substeps, tol, maxiter, ctypes.byref(info))
     elif integrator == "omelyan":
         rc = lib().sf_md_trajectory_omelyan(lat.handle, ALGOS[algo], nrhs, _ptr(phi), _ptr(mom), nsteps, dt, lam,
                                             tol, maxiter, ctypes.byref(info))
@@ -366,7 +371,8 @@ def md_trajectory(lat: Lattice, algo: str, phi, mom, nsteps: int, dt: float, tol
 
 
 def hmc_trajectory(lat: Lattice, algo: str, eta, mom, uniform: float, nsteps: int, dt: float,
-                   tol: float = 1e-10, maxiter: int = 10000, integrator: str = "leapfrog") -> dict:
+                   tol: float = 1e-10, maxiter: int = 10000, integrator: str = "leapfrog",
+                   gauge_substeps: int = 1) -> dict:
     """One HMC trajectory with the caller's random numbers: pseudo-fermions
     phi = Dhat eta from the Gaussian even-site fields eta (so S_f = |eta|^2 at
     the start), an MD trajectory from the momenta mom, and the Metropolis
@@ -378,7 +384,8 @@ def hmc_trajectory(lat: Lattice, algo: str, eta, mom, uniform: float, nsteps: in
     wilson_apply_block(lat, "dhat", "fp64", eta, phi)
     old = torch.empty((lat.T + 1) * lat.L ** 3 * 4 * 18, dtype=torch.float64, device=eta.device)
     get_links(lat, old)
-    d = md_trajectory(lat, algo, phi, mom, nsteps, dt, tol, maxiter, integrator=integrator)
+    d = md_trajectory(lat, algo, phi, mom, nsteps, dt, tol, maxiter, integrator=integrator,
+                      gauge_substeps=gauge_substeps)
     d["accepted"] = bool(uniform < math.exp(min(0.0, -d["dH"])))
     if not d["accepted"]:
         lat.set_links(old)

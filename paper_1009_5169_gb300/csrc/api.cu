@@ -2725,10 +2725,12 @@ sf_status sf_lattice_get_links(sf_lattice* lat, double* links) {
 }  // extern "C"
 
 namespace {
-// One MD trajectory; lam < 0: the leapfrog, else the second-order
-// minimum-norm integrator of Omelyan, Mryglod and Folk with parameter lam.
+// One MD trajectory; lam < 0: the leapfrog with the gauge force on m
+// substeps of each step (two time scales; m = 1 the plain leapfrog), else the
+// second-order minimum-norm integrator of Omelyan, Mryglod and Folk with
+// parameter lam.
 sf_status md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom, int nsteps,
-                        double dt, double lam, double tol, int maxiter, sf_md_info* info) {
+                        double dt, double lam, int m, double tol, int maxiter, sf_md_info* info) {
     bool noconv = false;
     sf_status st = guarded([&] {
         const auto t0 = std::chrono::steady_clock::now();
@@ -2760,18 +2762,27 @@ sf_status md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         int inner = 0, evals = 0;
         CK(launch_mom_fix(lat->L, lat->T, dM, s));
         const long long nmom = (long long)(fb / sizeof(double));
-        // P -= e (F_gauge + F_fermion)(U); returns S_f(U) = sum |X|^2
-        auto kick = [&](double e) {
+        // P -= e F_gauge(U)
+        auto kick_gauge = [&](double e) {
             CK(launch_gauge_force(lat->L, lat->T, lat->beta, lat->canon.as<double>(), nullptr, dM, e, s));
+            launches += 1;
+        };
+        // P -= e F_fermion(U); returns S_f(U) = sum |X|^2
+        auto kick_fermion = [&](double e) {
             sf_solve_info fi;
             const sf_status r = md_force_step(lat, algo, nrhs, dP, xs.as<double>(), ys.as<double>(), nullptr, dM, e,
                                               tol, maxiter, &fi);
             if (r == SF_ENOCONV) noconv = true;
             else if (r != SF_OK) throw SfError{r, g_err};
-            launches += 1 + fi.kernel_launches;
+            launches += fi.kernel_launches;
             inner += fi.iters_inner + fi.iters_inner_y;
             ++evals;
             return sumsq(lat, (long long)(xb / sizeof(double)), xs.as<double>(), 1.0);
+        };
+        // P -= e (F_gauge + F_fermion)(U); returns S_f(U)
+        auto kick = [&](double e) {
+            kick_gauge(e);
+            return kick_fermion(e);
         };
         auto gauge_action = [&](double* S) {
             const sf_status r = plaquette_action(lat, S);
@@ -2788,12 +2799,17 @@ sf_status md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
             launches += 2;
         };
         double sf_end;
-        if (lam < 0.0) {   // leapfrog
-            out.s_fermion[0] = kick(0.5 * dt);
+        if (lam < 0.0) {   // leapfrog; the gauge force on m substeps of dt / m (neighbouring half kicks merged)
+            const double h = dt / m;
+            kick_gauge(0.5 * h);
+            out.s_fermion[0] = kick_fermion(0.5 * dt);
             sf_end = out.s_fermion[0];
             for (int k = 0; k < nsteps; ++k) {
-                drift(dt);
-                sf_end = kick(k == nsteps - 1 ? 0.5 * dt : dt);
+                for (int j = 0; j < m; ++j) {
+                    drift(h);
+                    kick_gauge(k == nsteps - 1 && j == m - 1 ? 0.5 * h : h);
+                }
+                sf_end = kick_fermion(k == nsteps - 1 ? 0.5 * dt : dt);
             }
         } else {           // kick lam dt, drift dt/2, kick (1 - 2 lam) dt, drift dt/2, kick lam dt
             out.s_fermion[0] = kick(lam * dt);
@@ -2831,7 +2847,17 @@ extern "C" {
 
 sf_status sf_md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom, int nsteps,
                            double dt, double tol, int maxiter, sf_md_info* info) {
-    return md_trajectory(lat, algo, nrhs, phi, mom, nsteps, dt, -1.0, tol, maxiter, info);
+    return md_trajectory(lat, algo, nrhs, phi, mom, nsteps, dt, -1.0, 1, tol, maxiter, info);
+}
+
+sf_status sf_md_trajectory_two_scales(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom,
+                                      int nsteps, double dt, int gauge_substeps, double tol, int maxiter,
+                                      sf_md_info* info) {
+    if (gauge_substeps < 1 || gauge_substeps > 1000) {
+        g_err = "gauge_substeps must be in 1..1000";
+        return SF_EINVAL;
+    }
+    return md_trajectory(lat, algo, nrhs, phi, mom, nsteps, dt, -1.0, gauge_substeps, tol, maxiter, info);
 }
 
 sf_status sf_md_trajectory_omelyan(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom,
@@ -2840,7 +2866,7 @@ sf_status sf_md_trajectory_omelyan(sf_lattice* lat, sf_algo algo, int nrhs, cons
         g_err = "lambda must be in (0, 1/2)";
         return SF_EINVAL;
     }
-    return md_trajectory(lat, algo, nrhs, phi, mom, nsteps, dt, lambda, tol, maxiter, info);
+    return md_trajectory(lat, algo, nrhs, phi, mom, nsteps, dt, lambda, 1, tol, maxiter, info);
 }
 
 // ---------------------------------------------------------------- batches

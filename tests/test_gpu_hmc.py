@@ -1,6 +1,6 @@
 """GPU parity of the HMC trajectory pieces (gauge force, link update, the
-leapfrog and Omelyan trajectories around Alg. 2) against the FP64 oracle,
-through the C ABI.
+leapfrog, two-time-scale and Omelyan trajectories around Alg. 2) against the
+FP64 oracle, through the C ABI.
 
 Tolerances: the gauge force and the link exponential are single FP64
 evaluations (1e-12 / 1e-13 relative); the trajectory composes solves to
@@ -125,7 +125,54 @@ def test_md_trajectory_matches_oracle_omelyan(sf, mdcase, algo):
     lat.close()
 
 
-def test_omelyan_rejects_bad_lambda(sf, mdcase):
+@pytest.mark.parametrize("algo", ["mixed_dc", "cg_normal"])
+def test_md_trajectory_matches_oracle_two_scales(sf, mdcase, algo):
+    """The leapfrog with the gauge force on 3 substeps of each step against
+    the oracle's nested leapfrog; the fermion force is evaluated nsteps + 1
+    times."""
+    c = mdcase
+    L, T = c["L"], c["T"]
+    Uo, Po, h0, h1 = hmc.leapfrog_two_scales(c["U"], c["P"], c["phi"], L, T, c["theta"], c["kappa"], c["beta"],
+                                             3, 0.05, 3)
+    lat = _lat(sf, c["U"], L, T, c["theta"], c["kappa"], c["beta"])
+    mom = torch.from_numpy(c["P"].copy()).cuda()
+    info = sf.md_trajectory(lat, algo, torch.from_numpy(c["phi"]).cuda(), mom, 3, 0.05, tol=1e-12,
+                            gauge_substeps=3)
+    assert info["force_evals"] == 4
+    out = torch.empty(((T + 1) * L ** 3, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    sf.get_links(lat, out)
+    assert relerr(out.cpu().numpy(), Uo) <= 1e-9
+    assert relerr(mom.cpu().numpy(), Po) <= 1e-8
+    for k in range(3):
+        assert abs([info["kinetic"], info["s_gauge"], info["s_fermion"]][k][1] - h1[k]) <= 1e-9 * abs(h1[k])
+    assert abs(info["dH"] - (sum(h1) - sum(h0))) <= 1e-7
+    lat.close()
+
+
+def test_two_scales_with_one_substep_is_the_leapfrog(sf, mdcase):
+    """gauge_substeps = 1 runs the same kicks and drifts in the same order as
+    sf_md_trajectory: bitwise the same links and momenta."""
+    c = mdcase
+    L, T = c["L"], c["T"]
+    outs = []
+    for fn in ("leapfrog", "two_scales"):
+        lat = _lat(sf, c["U"], L, T, c["theta"], c["kappa"], c["beta"])
+        mom = torch.from_numpy(c["P"].copy()).cuda()
+        phi = torch.from_numpy(c["phi"]).cuda()
+        if fn == "leapfrog":
+            sf.md_trajectory(lat, "cg_normal", phi, mom, 2, 0.05, tol=1e-12)
+        else:
+            n = sf.lib().sf_md_trajectory_two_scales(lat.handle, sf.ALGOS["cg_normal"], 2, sf._ptr(phi),
+                                                     sf._ptr(mom), 2, 0.05, 1, 1e-12, 10000, None)
+            assert n == 0
+        out = torch.empty(((T + 1) * L ** 3, 4, 3, 3), dtype=torch.complex128, device="cuda")
+        sf.get_links(lat, out)
+        outs.append((out.cpu().numpy(), mom.cpu().numpy()))
+        lat.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_integrators_reject_bad_parameters(sf, mdcase):
     c = mdcase
     lat = _lat(sf, c["U"], c["L"], c["T"], c["theta"], c["kappa"], c["beta"])
     mom = torch.from_numpy(c["P"].copy()).cuda()
@@ -133,6 +180,9 @@ def test_omelyan_rejects_bad_lambda(sf, mdcase):
         with pytest.raises(sf.SFError):
             sf.md_trajectory(lat, "cg_normal", torch.from_numpy(c["phi"]).cuda(), mom, 1, 0.05,
                              integrator="omelyan", lam=lam)
+    for m in (0, -2, 1001):
+        with pytest.raises(sf.SFError):
+            sf.md_trajectory(lat, "cg_normal", torch.from_numpy(c["phi"]).cuda(), mom, 1, 0.05, gauge_substeps=m)
     assert np.array_equal(mom.cpu().numpy(), c["P"])
     lat.close()
 

@@ -1,10 +1,12 @@
 """Pins of the HMC trajectory oracle (gauge force, link exponential,
-leapfrog, the Omelyan integrator) against what the mathematics fixes: central
+leapfrog, the Omelyan integrator, the leapfrog on two time scales) against what the mathematics fixes: central
 finite differences of the plaquette action (with scipy's expm, not the
 oracle's exponential), closed forms of the exponential, the O(dt^2) energy
 error of both integrators and their time reversibility, the Omelyan
-integrator at lam = 1/2 reducing to the leapfrog, and its smaller energy
-error at the minimum-norm lam for the same number of force evaluations.  A
+integrator at lam = 1/2 and the two-scale leapfrog at one substep reducing
+to the leapfrog, and their smaller energy errors (the minimum-norm lam at
+the same force count; gauge substeps on a field whose gauge action
+dominates the error).  A
 wrong sign, a dropped staple or a wrong boundary rule in the gauge force
 breaks the finite differences; a wrong kick order or sign breaks the dt^2
 scaling and reversibility; a misplaced lam breaks the lam = 1/2 reduction or
@@ -176,3 +178,42 @@ def test_omelyan_beats_leapfrog_at_equal_force_count(mdcase):
     _, _, h0, h1 = _om(c, 4, 0.05)
     _, _, g0, g1 = _traj(c, 8, 0.025)
     assert abs(sum(h1) - sum(h0)) < 0.5 * abs(sum(g1) - sum(g0))
+
+
+def _ts(c, nsteps, dt, m, U=None, P=None):
+    return hmc.leapfrog_two_scales(c["U"] if U is None else U, c["P"] if P is None else P, c["phi"], c["L"],
+                                   c["T"], c["theta"], c["kappa"], c["beta"], nsteps, dt, m)
+
+
+def test_two_scales_with_one_substep_is_leapfrog(mdcase):
+    c = mdcase
+    Ua, Pa, a0, a1 = _ts(c, 3, 0.05, 1)
+    Ub, Pb, b0, b1 = _traj(c, 3, 0.05)
+    m = hmc.dynamic_mask(c["L"], c["T"])
+    assert np.max(np.abs(Ua - Ub)) < 1e-13
+    assert np.max(np.abs(Pa[m] - Pb[m])) < 1e-12
+
+
+def test_two_scales_second_order_and_reversible(mdcase):
+    c = mdcase
+    _, _, h0, h1 = _ts(c, 4, 0.05, 4)
+    _, _, g0, g1 = _ts(c, 8, 0.025, 4)
+    dh1, dh2 = sum(h1) - sum(h0), sum(g1) - sum(g0)
+    assert abs(dh1) > 1e-6
+    assert 3.2 < dh1 / dh2 < 4.8, (dh1, dh2)
+    U1, P1, _, _ = _ts(c, 3, 0.05, 3)
+    U2, P2, _, _ = _ts(c, 3, 0.05, 3, U=U1, P=-P1)
+    m = hmc.dynamic_mask(c["L"], c["T"])
+    assert np.max(np.abs(U2 - c["U"])) < 1e-10
+    assert np.max(np.abs(-P2[m] - c["P"][m])) < 1e-9
+
+
+def test_two_scales_shrink_the_gauge_error(mdcase):
+    """On this field the gauge force dominates the leapfrog's energy error
+    (the plaquette action moves by about 170 over the trajectory, the fermion
+    action by 2): four gauge substeps per fermion step cut |dH| several-fold
+    at the same number of fermion force evaluations."""
+    c = mdcase
+    _, _, a0, a1 = _ts(c, 4, 0.05, 1)
+    _, _, b0, b1 = _ts(c, 4, 0.05, 4)
+    assert abs(sum(b1) - sum(b0)) < 0.25 * abs(sum(a1) - sum(a0))
