@@ -180,6 +180,7 @@ struct sf_lattice {
     DevMem stage_f, stage_m;     // force and momentum staging (host F, mom)
     cudaStream_t side = nullptr; // device-to-host copies that overlap the compute stream
     cudaEvent_t side_ev = nullptr;
+    cudaEvent_t mom_ev = nullptr;  // md_force_step: the host momenta have reached stage_m
     int tune_TS[3] = {0, 0, 0}, tune_NR[3] = {0, 0, 0}, tune_pipe[3] = {0, 0, 0};
     struct Workspace* ws = nullptr;  // own solver workspace (created on first use)
     sf_cnn* cnn = nullptr;           // learned preconditioner for SF_SOLVE_FGCR_CNN (not owned)
@@ -2268,6 +2269,7 @@ void sf_lattice_destroy(sf_lattice* lat) {
         cudaStreamDestroy(lat->side);
     }
     if (lat->side_ev) cudaEventDestroy(lat->side_ev);
+    if (lat->mom_ev) cudaEventDestroy(lat->mom_ev);
     delete lat->ws;
     delete lat;
 }
@@ -2482,7 +2484,10 @@ void ensure_odd(Workspace& w) {
 
 // The force of Eq. (3) from the workspace's x64, xo64, y64, yo64 (even and
 // odd sites of X and Y): F = sum_i f[x_i, y_i] and / or mom -= eps F.
-void force_from_workspace(sf_lattice* lat, Workspace& w, double* F, double* mom, double eps) {
+// mom_staged: a host mom was already copied to stage_m on the side stream
+// (recorded by mom_ev)
+void force_from_workspace(sf_lattice* lat, Workspace& w, double* F, double* mom, double eps,
+                          bool mom_staged = false) {
     cudaStream_t s = lat->stream;
     const LaunchCfg& pl = w.cfg[0].per_lat[0];
     const size_t fbytes = (size_t)(lat->T + 1) * lat->L * lat->L * lat->L * 4 * 8 * sizeof(double);
@@ -2495,6 +2500,9 @@ void force_from_workspace(sf_lattice* lat, Workspace& w, double* F, double* mom,
     if (mom) {
         if (is_device_ptr(mom)) {
             dM = mom;
+        } else if (mom_staged) {
+            CK(cudaStreamWaitEvent(s, lat->mom_ev, 0));
+            dM = lat->stage_m.as<double>();
         } else {
             lat->stage_m.ensure(fbytes);
             CK(cudaMemcpyAsync(lat->stage_m.p, mom, fbytes, cudaMemcpyHostToDevice, s));
@@ -2581,6 +2589,20 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         const double* dphi = to_device(phi, bytes, lat->stage_in, s);
         CK(o.pack(pl, dphi, w.phi64.ptr(), s));
         w.launches += 1;
+        // host momenta go to the device on the side stream while the solves run
+        const bool host_out = (!is_device_ptr(X) || !is_device_ptr(Y));
+        const bool host_mom = (mom != nullptr && !is_device_ptr(mom));
+        if ((host_out || host_mom) && !lat->side) {
+            CK(cudaStreamCreateWithFlags(&lat->side, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&lat->side_ev, cudaEventDisableTiming));
+        }
+        if (host_mom) {
+            if (!lat->mom_ev) CK(cudaEventCreateWithFlags(&lat->mom_ev, cudaEventDisableTiming));
+            const size_t fbytes = (size_t)(lat->T + 1) * lat->L * lat->L * lat->L * 4 * 8 * sizeof(double);
+            lat->stage_m.ensure(fbytes);
+            CK(cudaMemcpyAsync(lat->stage_m.p, mom, fbytes, cudaMemcpyHostToDevice, lat->side));
+            CK(cudaEventRecord(lat->mom_ev, lat->side));
+        }
         // X = Dhat^-1 phi and its odd part; Y = Dhat^-dag X and its odd part
         auto run = [&](bool dag, const FieldBuf& rhs, FieldBuf& sol, FieldBuf& odd) {
             if (!fgcr && !glb && !blb && ci < 8) return w.solve(ci, dag, rhs, sol, tol, maxiter, false, &odd);
@@ -2600,10 +2622,6 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         }
         // host outputs: X and Y leave on the side stream while the Y solve and
         // the force run on the compute stream
-        if ((!is_device_ptr(X) || !is_device_ptr(Y)) && !lat->side) {
-            CK(cudaStreamCreateWithFlags(&lat->side, cudaStreamNonBlocking));
-            CK(cudaEventCreateWithFlags(&lat->side_ev, cudaEventDisableTiming));
-        }
         auto out_async = [&](double* dst, FieldBuf& f, DevMem& stage) {
             double* dv = out_device(dst, bytes, stage);
             CK(o.unpack(pl, f.ptr(), dv, s));
@@ -2617,13 +2635,16 @@ sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* p
         if (!normal) ry = run(true, w.x64, w.y64, w.yo64);
         out_async(Y, w.y64, lat->stage_out2);
         w.launches += 2;
-        force_from_workspace(lat, w, F, mom, eps);
+        force_from_workspace(lat, w, F, mom, eps, host_mom);
         CK(cudaStreamSynchronize(s));
         if (lat->side) CK(cudaStreamSynchronize(lat->side));
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         fill_info(info, rx, &ry, 0, nrhs, secs, w.launches);
         if (!rx.converged || !ry.converged) noconv = true;
     });
+    // on a failure, copies the side stream still holds from or to the
+    // caller's host buffers end before the call returns
+    if (st != SF_OK && lat != nullptr && lat->side) cudaStreamSynchronize(lat->side);
     if (st == SF_OK && noconv) {
         g_err = "solver stopped above tolerance";
         return SF_ENOCONV;
