@@ -397,8 +397,8 @@ sf_status plaquette_action_noalloc(int L, int T, double beta, const double* link
 const char* sf_last_error(void);
 
 /* ---- batches: several lattices (any sizes) solved by one launch per kernel
- * and group of lattices (spec batching of many independent fields; the
- * paper solves its five equations per field, Sec. 3.2).  At create the
+ * and group of lattices (an addition: the paper solves the five equations
+ * of one field, Sec. 3.2, and has no batching over fields).  At create the
  * lattices are grouped so that each group's inner-loop working set (FP32
  * links and six FP32 vectors per RHS) fits in three quarters of the L2 cache;
  * a lattice larger than that forms a group of its own.  Groups are solved one
