@@ -225,8 +225,8 @@ def test_md_force_step_matches_separate_calls(sf, algo):
 @pytest.mark.parametrize("algo", ["cg_normal", "mixed_dc"])
 def test_md_force_step_host_buffers(sf, algo):
     """Alg. 2 in one call with host (pageable and pinned) buffers gives bitwise
-    the device-buffer results (the X, Y copies leave on a side stream while
-    the Y solve and the force run)."""
+    the device-buffer results (the momenta arrive and the X, Y copies leave
+    on a side stream while the solves and the force run)."""
     L, T, eps, kappa, theta = 6, 7, 0.3, 0.13, 0.5
     U = inputs.links(L, T, eps, 151)
     phi = inputs.sources(L, T, 3, 152)
