@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -147,6 +148,14 @@ struct FieldBuf {
 };
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// |r| / |b| from the squared norms; NaN when either is not finite (a
+// corrupted input reports as such, not as converged), 0 for a zero b (the
+// solution is then exactly zero).
+double rel_resid(double rr, double bb) {
+    if (!std::isfinite(rr) || !std::isfinite(bb)) return std::numeric_limits<double>::quiet_NaN();
+    return bb > 0 ? sqrt(rr / bb) : 0.0;
+}
 
 // SF_NO_GRAPH=1 runs the solver loops without CUDA graphs (every kernel
 // launched from the host; for profilers that cannot look into conditional
@@ -792,7 +801,7 @@ struct Workspace {
         CK(cudaMemcpyAsync(rr.data(), nrm_rr.p, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
         CK(cudaMemcpyAsync(bb.data(), nrm_bb.p, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
-        for (size_t i = 0; i < n; ++i) out[i] = bb[i] > 0 ? sqrt(rr[i] / bb[i]) : 0.0;
+        for (size_t i = 0; i < n; ++i) out[i] = rel_resid(rr[i], bb[i]);
         return out;
     }
 
@@ -931,7 +940,7 @@ struct Workspace {
         for (size_t i = 0; i < n; ++i) {
             res.sweeps[i] = out[i].sweeps;
             res.inner[i] = out[i].inner_iters;
-            res.resid[i] = out[i].bb > 0 ? sqrt(out[i].rr / out[i].bb) : 0.0;
+            res.resid[i] = rel_resid(out[i].rr, out[i].bb);
             const bool ok = (out[i].bb == 0.0) || (out[i].rr <= out[i].tol2 * out[i].bb);
             if (!ok) res.converged = false;
         }
@@ -1182,7 +1191,7 @@ Workspace::Result Workspace::fgcr(bool use_cnn, bool dag, const FieldBuf& phi, F
     res.resid.resize(n);
     bool ok = true;
     for (int i = 0; i < n; ++i) {
-        res.resid[i] = bb[i] > 0 ? sqrt(rt[i] / bb[i]) : 0.0;
+        res.resid[i] = rel_resid(rt[i], bb[i]);
         if (!(rt[i] <= tol * tol * bb[i])) ok = false;
     }
     if (ok) return res;
@@ -1404,7 +1413,7 @@ Workspace::Result Workspace::fgcr_mixed(bool use_cnn, bool dag, const FieldBuf& 
     res.resid.resize(n);
     bool ok = true;
     for (int i = 0; i < n; ++i) {
-        res.resid[i] = bb[i] > 0 ? sqrt(rr[i] / bb[i]) : 0.0;
+        res.resid[i] = rel_resid(rr[i], bb[i]);
         if (!(rr[i] <= tol * tol * bb[i])) ok = false;
     }
     if (ok) return res;
@@ -1621,7 +1630,7 @@ Workspace::Result Workspace::gl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf
         CK(cudaStreamSynchronize(s));
         bool ok = true;
         for (int i = 0; i < n; ++i)
-            if (!(rt[i] <= tol * tol * bb[i]) && bb[i] > 0.0) ok = false;
+            if (!(bb[i] == 0.0 || rt[i] <= tol * tol * bb[i])) ok = false;
         if (ok || cycle + 1 >= max_restarts) {
             res.converged = ok;
             break;
@@ -1630,7 +1639,7 @@ Workspace::Result Workspace::gl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf
     }
     for (int i = 0; i < n; ++i) {
         res.sweeps[i] = calls;
-        res.resid[i] = bb[i] > 0 ? sqrt(rt[i] / bb[i]) : 0.0;
+        res.resid[i] = rel_resid(rt[i], bb[i]);
     }
     return res;
 }
@@ -1802,7 +1811,7 @@ Workspace::Result Workspace::bl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf
         CK(cudaStreamSynchronize(s));
         bool ok = true;
         for (int i = 0; i < n; ++i)
-            if (!(rt[i] <= tol * tol * bb[i]) && bb[i] > 0.0) ok = false;
+            if (!(bb[i] == 0.0 || rt[i] <= tol * tol * bb[i])) ok = false;
         if (ok || cycle + 1 >= max_restarts || iters >= maxiter) {
             res.converged = ok;
             break;
@@ -1812,7 +1821,7 @@ Workspace::Result Workspace::bl_bicgstab(bool dag, const FieldBuf& phi, FieldBuf
     for (int i = 0; i < n; ++i) {
         res.sweeps[i] = cycles;
         res.inner[i] = iters;
-        res.resid[i] = bb[i] > 0 ? sqrt(rt[i] / bb[i]) : 0.0;
+        res.resid[i] = rel_resid(rt[i], bb[i]);
     }
     return res;
 }
@@ -1949,8 +1958,8 @@ Workspace::Result Workspace::bl_bicgstab_graph(bool dag, const FieldBuf& phi, Fi
     res.resid.assign(n, 0.0);
     res.converged = true;
     for (int i = 0; i < n; ++i) {
-        res.resid[i] = h.bb[i] > 0 ? sqrt(h.rr[i] / h.bb[i]) : 0.0;
-        if (!(h.rr[i] <= tol * tol * h.bb[i]) && h.bb[i] > 0.0) res.converged = false;
+        res.resid[i] = rel_resid(h.rr[i], h.bb[i]);
+        if (!(h.bb[i] == 0.0 || h.rr[i] <= tol * tol * h.bb[i])) res.converged = false;
     }
     continue_per_rhs(*this, res, dag, phi, x, tol, maxiter);
     return res;
@@ -2092,8 +2101,8 @@ Workspace::Result Workspace::gl_bicgstab_graph(bool dag, const FieldBuf& phi, Fi
     res.converged = true;
     for (int i = 0; i < n; ++i) {
         res.inner[i] = oo[i].inner_iters;
-        res.resid[i] = h.bb[i] > 0 ? sqrt(h.rr[i] / h.bb[i]) : 0.0;
-        if (!(h.rr[i] <= tol * tol * h.bb[i]) && h.bb[i] > 0.0) res.converged = false;
+        res.resid[i] = rel_resid(h.rr[i], h.bb[i]);
+        if (!(h.bb[i] == 0.0 || h.rr[i] <= tol * tol * h.bb[i])) res.converged = false;
     }
     continue_per_rhs(*this, res, dag, phi, x, tol, maxiter);
     return res;

@@ -381,6 +381,52 @@ def test_zero_sources(sf, algo):
     lat.close()
 
 
+@pytest.mark.parametrize("algo", ["bicgstab", "mixed_dc", "mixed_dc_half", "cg_normal"])
+def test_nan_source_ends_that_rhs_only(sf, algo):
+    """A NaN in one right-hand side (a corrupted input): its residual is not
+    finite, so its iteration stops at once (NaN fails every stop-or-continue
+    comparison on the side of stopping); the solve returns SF_ENOCONV instead
+    of looping, and the other right-hand sides, whose iterations are
+    independent, still meet the tolerance."""
+    L, T = 4, 5
+    U, lat = _lattice(sf, L, T, 0.3, 0.12, 0.5, seed=145)
+    phi = inputs.sources(L, T, 3, 146)
+    phi[1, 7, 2, 1] = np.nan
+    pd = torch.from_numpy(phi).cuda()
+    X, Y = torch.empty_like(pd), torch.empty_like(pd)
+    info = sf.solve_block(lat, algo, pd, X, Y, tol=1e-10, maxiter=500, allow_noconv=True)
+    assert info["status"] == "SF_ENOCONV"
+    r = np.asarray(info["true_resid"])
+    assert not np.isfinite(r[1])
+    Xn = X.cpu().numpy()
+    for i in (0, 2):
+        assert r[i] <= 1e-10
+        ro = oracle.true_residual(U, phi[i:i + 1], Xn[i:i + 1], L, T, 0.5, 0.12)
+        assert ro[0] <= 1.05e-10
+    lat.close()
+
+
+@pytest.mark.parametrize("algo", ["bicgstab", "mixed_dc", "cg_normal"])
+def test_iteration_cap_returns_best_iterate(sf, algo):
+    """maxiter (the inner iterations of each sweep) far below what the solve
+    needs: one iteration per sweep, so the sweep cap ends the solve with
+    SF_ENOCONV, the iterate reached so far in X and its true residual
+    reported (finite, below the start, above the tolerance), as the oracle
+    recomputes it."""
+    L, T = 6, 6
+    U, lat = _lattice(sf, L, T, 0.3, 0.13, 0.5, seed=147)
+    phi = inputs.sources(L, T, 2, 148)
+    pd = torch.from_numpy(phi).cuda()
+    X, Y = torch.empty_like(pd), torch.empty_like(pd)
+    info = sf.solve_block(lat, algo, pd, X, Y, tol=1e-10, maxiter=1, allow_noconv=True)
+    assert info["status"] == "SF_ENOCONV"
+    r = np.asarray(info["true_resid"])
+    assert np.all(np.isfinite(r)) and np.all(r > 1e-10) and np.all(r < 1.0)
+    ro = oracle.true_residual(U, phi, X.cpu().numpy(), L, T, 0.5, 0.13)
+    assert np.allclose(ro, r, rtol=1e-6, atol=0)
+    lat.close()
+
+
 def test_single_time_slice(sf):
     """T = 2: one fermion time slice, every time hop dropped (Dirichlet on
     both sides); apply and the mixed solve against the oracle."""
