@@ -229,3 +229,30 @@ def test_tcgen05_convolutions_match_mma_sync(sf, L, T):
     lat.close()
     assert frob(outs["tcgen05"], outs["mma_sync"]) <= 5e-3, frob(outs["tcgen05"], outs["mma_sync"])
     assert frob(grads["tcgen05"], grads["mma_sync"]) <= 2e-2, frob(grads["tcgen05"], grads["mma_sync"])
+
+
+def test_trained_network_checkpoint_round_trip(sf, tmp_path):
+    """A network trained a few steps, written to a checkpoint with the links
+    and sources and read back into a new network: bitwise the same
+    parameters and forward output."""
+    from paper_1009_5169_gb300 import checkpoint
+    L, T, hidden = 4, 6, 16
+    U = inputs.links(L, T, 0.3, 311)
+    r = inputs.sources(L, T, 2, 312)
+    net = sf.Cnn(hidden, inputs.cnn_init_params(hidden, 313))
+    lat = sf.Lattice(L, T, 0.5, 0.13, 4.52, U)
+    for _ in range(3):
+        net.train_step(lat, r, None, 1e-3)
+    path = str(tmp_path / "net.npz")
+    checkpoint.save_cnn(path, net, meta={"steps": 3, "seed": 313}, links=U, sources=r)
+    net2 = checkpoint.load_cnn(path)
+    c = checkpoint.load(path)
+    assert c["meta"]["steps"] == 3 and np.array_equal(c["links"], U)
+    assert np.array_equal(net2.params(), net.params())
+    o1, o2 = np.empty_like(r), np.empty_like(r)
+    net.forward(lat, r, o1)
+    net2.forward(lat, r, o2)
+    assert np.array_equal(o1, o2)
+    lat.close()
+    net.close()
+    net2.close()
