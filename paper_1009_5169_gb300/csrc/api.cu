@@ -28,6 +28,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "blocksolve.h"
 #include "sf_kernels.h"
 #include "sf_lattice.h"
@@ -148,6 +150,15 @@ struct FieldBuf {
 };
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// A named NVTX range for the duration of a scope (host side: visible in a
+// profiler's timeline around the work a call enqueues; free without one).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // |r| / |b| from the squared norms; NaN when either is not finite (a
 // corrupted input reports as such, not as converged), 0 for a zero b (the
@@ -2284,6 +2295,7 @@ void sf_lattice_destroy(sf_lattice* lat) {
 }
 
 sf_status wilson_apply_block(sf_lattice* lat, sf_op op, sf_prec prec, int nrhs, const double* in, double* out) {
+    NvtxRange nvtx_("sf wilson_apply_block");
     return guarded([&] {
         REQUIRE(lat != nullptr && in != nullptr && out != nullptr, "NULL argument");
         REQUIRE(op >= SF_OP_DHAT && op <= SF_OP_HOP_OE, "bad op");
@@ -2426,6 +2438,7 @@ int algo_index(sf_algo a) {
 
 sf_status solve_block(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* X, double* Y, double tol,
                       int maxiter, sf_solve_info* info) {
+    NvtxRange nvtx_("sf solve_block");
     bool noconv = false;
     sf_status st = guarded([&] {
         const auto t0 = std::chrono::steady_clock::now();
@@ -2548,6 +2561,7 @@ sf_status fermion_force_resident(sf_lattice* lat, int nrhs, double* F) {
 
 sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double* Y, double* F, double* mom,
                         double eps) {
+    NvtxRange nvtx_("sf fermion_force");
     return guarded([&] {
         REQUIRE(lat != nullptr && X != nullptr && Y != nullptr, "NULL argument");
         REQUIRE(F != nullptr || mom != nullptr, "F and mom are both NULL");
@@ -2574,6 +2588,7 @@ sf_status fermion_force(sf_lattice* lat, int nrhs, const double* X, const double
 
 sf_status md_force_step(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* X, double* Y,
                         double* F, double* mom, double eps, double tol, int maxiter, sf_solve_info* info) {
+    NvtxRange nvtx_("sf md_force_step");
     bool noconv = false;
     sf_status st = guarded([&] {
         const auto t0 = std::chrono::steady_clock::now();
@@ -2761,6 +2776,7 @@ namespace {
 // parameter lam.
 sf_status md_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* phi, double* mom, int nsteps,
                         double dt, double lam, int m, double tol, int maxiter, sf_md_info* info) {
+    NvtxRange nvtx_("sf md_trajectory");
     bool noconv = false;
     sf_status st = guarded([&] {
         const auto t0 = std::chrono::steady_clock::now();
@@ -2991,6 +3007,7 @@ sf_status sf_batch_create(sf_batch** out, int nlat, sf_lattice* const* lats, int
 
 sf_status sf_batch_solve(sf_batch* b, sf_algo algo, const double* const* phi, double* const* X, double* const* Y,
                          double tol, int maxiter, sf_solve_info* info) {
+    NvtxRange nvtx_("sf sf_batch_solve");
     bool noconv = false;
     sf_status st = guarded([&] {
         const auto t0 = std::chrono::steady_clock::now();
