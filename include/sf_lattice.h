@@ -298,6 +298,24 @@ sf_status sf_md_trajectory_two_scales(sf_lattice* lat, sf_algo algo, int nrhs, c
                                       int nsteps, double dt, int gauge_substeps, double tol, int maxiter,
                                       sf_md_info* info);
 
+typedef enum { SF_MD_LEAPFROG = 0, SF_MD_OMELYAN = 1 } sf_md_integrator;
+
+/* One HMC trajectory (the algorithm the paper runs, Sec. 2) with the
+ * caller's random numbers: pseudo-fermions phi = Dhat eta from the Gaussian
+ * even-site fields eta (nrhs of them, host or device; S_f = |eta|^2 at the
+ * start), the MD trajectory of sf_md_trajectory_two_scales (leapfrog,
+ * gauge_substeps >= 1) or sf_md_trajectory_omelyan (lambda) from the momenta
+ * mom (in / out, host or device), then the Metropolis test: *accepted = 1 if
+ * uniform < exp(-dH), else 0 and the links are put back to those of the
+ * start.  mom keeps its end-of-trajectory values either way (a new
+ * trajectory draws new momenta).  SF_EINVAL on a NULL pointer, an unknown
+ * integrator or a parameter out of range; SF_ENOCONV if a solve stopped above
+ * tol (the test is still applied). */
+sf_status sf_hmc_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* eta, double* mom,
+                            double uniform, sf_md_integrator integrator, int nsteps, double dt,
+                            int gauge_substeps, double lambda, double tol, int maxiter, sf_md_info* info,
+                            int* accepted);
+
 /* One launch of the hopping-term kernel H_oe (out_parity 1) or H_eo
  * (out_parity 0) for nrhs fields in precision prec, on the lattice's
  * resident operand and result buffers (those wilson_apply_block last packed;

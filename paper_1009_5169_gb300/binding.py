@@ -11,7 +11,6 @@ tensors (host or CUDA), complex128 in the canonical layouts of the header:
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 from dataclasses import dataclass, field
 from typing import List, Optional, Sequence
@@ -100,6 +99,8 @@ def lib() -> ctypes.CDLL:
         L.sf_md_trajectory.argtypes = [vp, i, i, vp, vp, i, d, d, i, ctypes.POINTER(MdInfo)]
         L.sf_md_trajectory_omelyan.argtypes = [vp, i, i, vp, vp, i, d, d, d, i, ctypes.POINTER(MdInfo)]
         L.sf_md_trajectory_two_scales.argtypes = [vp, i, i, vp, vp, i, d, i, d, i, ctypes.POINTER(MdInfo)]
+        L.sf_hmc_trajectory.argtypes = [vp, i, i, vp, vp, d, i, i, d, i, d, d, i, ctypes.POINTER(MdInfo),
+                                        ctypes.POINTER(ctypes.c_int)]
         L.plaquette_action_noalloc.argtypes = [i, i, d, vp, vp, i, vp]
         L.plaquette_action_noalloc.restype = ctypes.c_int
         L.sf_cnn_num_params.argtypes = [i]
@@ -370,25 +371,29 @@ def md_trajectory(lat: Lattice, algo: str, phi, mom, nsteps: int, dt: float, tol
     return d
 
 
+INTEGRATORS = {"leapfrog": 0, "omelyan": 1}
+
+
 def hmc_trajectory(lat: Lattice, algo: str, eta, mom, uniform: float, nsteps: int, dt: float,
                    tol: float = 1e-10, maxiter: int = 10000, integrator: str = "leapfrog",
-                   gauge_substeps: int = 1) -> dict:
-    """One HMC trajectory with the caller's random numbers: pseudo-fermions
-    phi = Dhat eta from the Gaussian even-site fields eta (so S_f = |eta|^2 at
-    the start), an MD trajectory from the momenta mom, and the Metropolis
-    test: accepted if uniform < exp(-dH), else the links are restored.
-    Returns the md_trajectory dict with "accepted"."""
-    import torch
-
-    phi = torch.empty_like(eta)
-    wilson_apply_block(lat, "dhat", "fp64", eta, phi)
-    old = torch.empty((lat.T + 1) * lat.L ** 3 * 4 * 18, dtype=torch.float64, device=eta.device)
-    get_links(lat, old)
-    d = md_trajectory(lat, algo, phi, mom, nsteps, dt, tol, maxiter, integrator=integrator,
-                      gauge_substeps=gauge_substeps)
-    d["accepted"] = bool(uniform < math.exp(min(0.0, -d["dH"])))
-    if not d["accepted"]:
-        lat.set_links(old)
+                   gauge_substeps: int = 1, lam: float = OMELYAN_LAMBDA, allow_noconv: bool = False) -> dict:
+    """One HMC trajectory with the caller's random numbers (sf_hmc_trajectory):
+    pseudo-fermions phi = Dhat eta, an MD trajectory from the momenta mom and
+    the Metropolis test with the uniform number.  Returns the md_trajectory
+    dict with "accepted"."""
+    nrhs = _nrhs_of(eta, lat.Vh * 24 * 8)
+    _check_size(mom, _mom_bytes(lat), "mom")
+    if integrator not in INTEGRATORS:
+        raise ValueError(f"integrator must be leapfrog or omelyan, got {integrator!r}")
+    info = MdInfo()
+    acc = ctypes.c_int()
+    rc = lib().sf_hmc_trajectory(lat.handle, ALGOS[algo], nrhs, _ptr(eta), _ptr(mom), uniform,
+                                 INTEGRATORS[integrator], nsteps, dt, gauge_substeps, lam, tol, maxiter,
+                                 ctypes.byref(info), ctypes.byref(acc))
+    _check(rc, allow_noconv)
+    d = info.as_dict()
+    d["status"] = STATUS[rc]
+    d["accepted"] = bool(acc.value)
     return d
 
 

@@ -2915,6 +2915,59 @@ sf_status sf_md_trajectory_omelyan(sf_lattice* lat, sf_algo algo, int nrhs, cons
     return md_trajectory(lat, algo, nrhs, phi, mom, nsteps, dt, lambda, 1, tol, maxiter, info);
 }
 
+sf_status sf_hmc_trajectory(sf_lattice* lat, sf_algo algo, int nrhs, const double* eta, double* mom, double uniform,
+                            sf_md_integrator integrator, int nsteps, double dt, int gauge_substeps, double lambda,
+                            double tol, int maxiter, sf_md_info* info, int* accepted) {
+    NvtxRange nvtx_("sf hmc_trajectory");
+    if (lat == nullptr || eta == nullptr || mom == nullptr || accepted == nullptr) {
+        g_err = "NULL argument";
+        return SF_EINVAL;
+    }
+    if (integrator != SF_MD_LEAPFROG && integrator != SF_MD_OMELYAN) {
+        g_err = "unknown integrator";
+        return SF_EINVAL;
+    }
+    if (integrator == SF_MD_OMELYAN && !(lambda > 0.0 && lambda < 0.5)) {
+        g_err = "lambda must be in (0, 1/2)";
+        return SF_EINVAL;
+    }
+    if (integrator == SF_MD_LEAPFROG && (gauge_substeps < 1 || gauge_substeps > 1000)) {
+        g_err = "gauge_substeps must be in 1..1000";
+        return SF_EINVAL;
+    }
+    *accepted = 0;
+    DevMem phi, old;
+    sf_status st = guarded([&] {
+        check_nrhs(nrhs);
+        CK(cudaSetDevice(lat->device));
+        phi.ensure((size_t)nrhs * lat->Vh * 24 * sizeof(double));
+        old.ensure(lat->links_bytes());
+        CK(cudaMemcpyAsync(old.p, lat->canon.p, lat->links_bytes(), cudaMemcpyDeviceToDevice, lat->stream));
+    });
+    if (st != SF_OK) return st;
+    // phi = Dhat eta: S_f = |eta|^2 at the start of the trajectory
+    st = wilson_apply_block(lat, SF_OP_DHAT, SF_FP64, nrhs, eta, phi.as<double>());
+    if (st != SF_OK) return st;
+    sf_md_info mi;
+    st = md_trajectory(lat, algo, nrhs, phi.as<double>(), mom, nsteps, dt,
+                       integrator == SF_MD_OMELYAN ? lambda : -1.0,
+                       integrator == SF_MD_OMELYAN ? 1 : gauge_substeps, tol, maxiter, &mi);
+    if (st != SF_OK && st != SF_ENOCONV) return st;
+    if (info) *info = mi;
+    // Metropolis: accept with probability min(1, exp(-dH)) given the caller's uniform number
+    const bool acc = uniform < std::exp(std::min(0.0, -mi.dH));
+    const sf_status rs = guarded([&] {
+        if (!acc) {   // back to the links at the start, and their prepared copies
+            CK(cudaMemcpyAsync(lat->canon.p, old.p, lat->links_bytes(), cudaMemcpyDeviceToDevice, lat->stream));
+            prepare_links(lat);
+        }
+        CK(cudaStreamSynchronize(lat->stream));
+    });
+    if (rs != SF_OK) return rs;
+    *accepted = acc ? 1 : 0;
+    return st;
+}
+
 // ---------------------------------------------------------------- batches
 }  // extern "C"
 

@@ -216,8 +216,9 @@ def test_md_trajectory_reversible_and_second_order(sf):
 
 
 def test_hmc_trajectory_metropolis(sf):
-    """Accepted: the links moved; rejected (uniform above exp(-dH)): the links
-    are restored exactly."""
+    """sf_hmc_trajectory (phi = Dhat eta, MD, Metropolis in the library).
+    Accepted: the links moved; rejected (uniform above exp(-dH)): the links
+    are restored exactly, for the leapfrog and the Omelyan integrator."""
     L, T = 4, 5
     U = inputs.links(L, T, 0.25, 131)
     P = inputs.su3_directions(((T + 1) * L ** 3, 4), 132)
@@ -233,4 +234,13 @@ def test_hmc_trajectory_metropolis(sf):
     assert not d["accepted"]
     sf.get_links(lat, out)
     assert np.array_equal(out.cpu().numpy(), U)
+    # the Omelyan integrator through the same call; rejected: the links are restored exactly
+    d = sf.hmc_trajectory(lat, "cg_normal", eta, torch.from_numpy(P.copy()).cuda(), 1.0 + 1e-9, 2, 0.05,
+                          integrator="omelyan")
+    assert not d["accepted"] and d["force_evals"] == 5
+    sf.get_links(lat, out)
+    assert np.array_equal(out.cpu().numpy(), U)
+    with pytest.raises(sf.SFError):
+        sf.hmc_trajectory(lat, "cg_normal", eta, torch.from_numpy(P.copy()).cuda(), 0.5, 2, 0.05,
+                          integrator="omelyan", lam=0.6)
     lat.close()
